@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the CG hot path on the paper-sized system.
+
+Workload: the Q1 hexahedral FEM matrix of a 50^3-element cube (N = 132651,
+NNZ = 3442951, the sizes of the paper's Section IV matrix), nu = 1 air with
+seeded iron blobs at nu = 1e-3, b = A x* for a seeded smooth x*, x0 = 0.
+A step is one FP64 CG solve to ||r|| <= 1e-8 ||b|| through the C ABI
+(one persistent kernel launch).  The L2 cache is flushed (a 2x L2 buffer
+is written) before every timed solve, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbcg|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU FP64
+oracle (serial C) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ms per solve to rel. residual 1e-8; SpMV HBM GB/s; chosen form vs FP64 CG"
+UNIT = "ms/solve"
+TOL = 1e-8
+WORKLOAD = ("q1-50^3 Q1 hex FEM, nu 1 / 1e-3 iron blobs (contrast 1e3), N=132651, NNZ=3442951, "
+            "b = A x*, x0 = 0, FP64 CG to rel. residual 1e-8")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gbcg", "reference"], default="gbcg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 100^3 SpMV roofline, the Jacobi form and the CPU baseline")
+    return ap.parse_args()
+
+
+def bytes_per_iteration(n: int, nnz: int, precond: bool) -> int:
+    """Algorithmic bytes of one fused CG iteration: CSR stream (12 NNZ + 4(N+1))
+    plus 11 FP64 vector passes (88 N); Jacobi adds a read of 1/diag and a write
+    of z (16 N)."""
+    return 12 * nnz + 4 * (n + 1) + 88 * n + (16 * n if precond else 0)
+
+
+def flops_per_iteration(n: int, nnz: int, precond: bool) -> int:
+    """The paper's count for one CG iteration (Table I): 2 NNZ + 10 N; Jacobi adds 3 N."""
+    return 2 * nnz + 10 * n + (3 * n if precond else 0)
+
+
+# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
+# clock x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def spmv_bytes(n: int, nnz: int) -> int:
+    """Algorithmic bytes of y = A x: CSR stream, x read once, y written once."""
+    return 12 * nnz + 4 * (n + 1) + 16 * n
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic(kernel: str) -> dict | None:
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
+    summary was taken on the current kernel source (hash match), else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_1107_0538_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        h.update(open(os.path.join(src, f), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
+            return {"dram_bytes": float(parts[2]), "units": float(parts[3])}
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args) -> None:
+    """The oracle (serial C, FP64) on the same workload, on the host cores."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1107_0538_gb300 import problems
+    pr = problems.cube_blobs(50)
+    times, iters = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.cg(pr.A, pr.b, tol=TOL)
+        dt = (time.perf_counter() - t0) * 1e3
+        assert r["status"] == oracle.OK
+        iters = r["iters"]
+        if i >= args.warmup:
+            times.append(dt)
+    v = sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": pr.A.n, "nnz": pr.A.nnz,
+                                        "tol": TOL, "iters": iters},
+        "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"full serial FP64 CG solves of the same system ({iters} iterations each)"},
+        "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gbcg(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_1107_0538_gb300 import gbcg, problems
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbcg.lib()
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    l2 = int(getattr(props, "L2_cache_size", 126 * 2 ** 20))
+
+    pr = problems.cube_blobs(50)
+    n, nnz = pr.A.n, pr.A.nnz
+    flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_solves(solver, b, x, count, record):
+        out = []
+        for _ in range(count):
+            x.zero_()
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solver.solve(b, x, tol=TOL)
+            e1.record(stream)
+            e1.synchronize()
+            if info.status != gbcg.CG_OK:
+                raise RuntimeError(f"solve failed: {gbcg.cg_strerror(info.status)}")
+            if record:
+                out.append((e0.elapsed_time(e1), info))
+        return out
+
+    # ---------------------------------------------------- FP64 CG (the step)
+    solver = gbcg.Solver(pr.A)
+    b = torch.from_numpy(pr.b).to(dev)
+    x = torch.zeros_like(b)
+    timed_solves(solver, b, x, args.warmup, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        res = timed_solves(solver, b, x, args.steps, True)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(t for t, _ in res)
+    kern_ms = [i.kernel_ms for _, i in res]
+    iters = res[-1][1].iters
+    relres_true = res[-1][1].relres_true
+    launches = sum(i.launches for _, i in res)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = total_ms / (args.steps * world)
+
+    bpi = bytes_per_iteration(n, nnz, False)
+    fpi = flops_per_iteration(n, nnz, False)
+    kern_s = statistics.mean(kern_ms) / 1e3
+    achieved_tflops = iters * fpi / kern_s / 1e12
+    achieved_gbs = iters * bpi / kern_s / 1e9
+    tr = ncu_traffic("cg_solve_kernel")
+    roofline = {
+        "bound": "alu", "kernel": "cg_solve_kernel", "achieved": round(achieved_tflops, 4),
+        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+        "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+        "traffic": (round(tr["dram_bytes"] / tr["units"] * iters) if tr else None),
+        "algorithmic_flops_per_launch": iters * fpi,
+        "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
+                     "algorithmic_bytes_per_launch": iters * bpi,
+                     "note": "53.5 MB per iteration stays in the 126 MB L2; HBM is read once per solve"},
+    }
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "tol": TOL, "iters": iters,
+                   "relres_true": relres_true, "l2_flush": "2x L2 buffer written before each solve",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "solve_kernel_ms": round(statistics.mean(kern_ms), 4)},
+        "roofline": roofline,
+        "gpu_launches": launches,
+    }
+
+    # ------------------------------------------------------------- e2e
+    bh = torch.from_numpy(pr.b.copy()).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    bn, xn = bh.numpy(), xh.numpy()
+    for _ in range(args.warmup):
+        xn[:] = 0.0
+        solver.solve_host(bn, xn, TOL)
+    e2e = []
+    for _ in range(args.steps):
+        xn[:] = 0.0
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = solver.solve_host(bn, xn, TOL)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+        assert info.status == gbcg.CG_OK
+    line["e2e"] = {"value": round(sum(e2e) / len(e2e), 4), "unit": UNIT,
+                   "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n + 40,
+                   "api": "cg_solve_host (pinned host b, x)"}
+    line["clocks"] = clk.summary()
+    solver.close()
+
+    if not args.no_extras:
+        # --------------------------------------------- Jacobi-PCG form
+        ps = gbcg.Solver(pr.A, precond=gbcg.CG_PRECOND_JACOBI)
+        timed_solves(ps, b, x, 2, False)
+        pres = timed_solves(ps, b, x, max(3, args.steps // 2), True)
+        p_ms = statistics.mean(t for t, _ in pres)
+        ps.close()
+        line["forms"] = {
+            "fp64_cg": {"ms_per_solve": round(ms_per_step, 4), "iters": iters},
+            "jacobi_pcg": {"ms_per_solve": round(p_ms, 4), "iters": pres[-1][1].iters,
+                           "speedup_vs_fp64_cg": round(ms_per_step / p_ms, 3)},
+        }
+        # -------------------------------------- SpMV roofline at 100^3 (HBM)
+        big = problems.cube_blobs(100)
+        bs = gbcg.Solver(big.A)
+        xb = torch.from_numpy(np.random.default_rng(0).standard_normal(big.A.n)).to(dev)
+        yb = torch.empty_like(xb)
+        for _ in range(3):
+            bs.spmv(xb, yb)
+        ts = []
+        for _ in range(20):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bs.spmv(xb, yb)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t_med = statistics.median(ts) / 1e3
+        sb = spmv_bytes(big.A.n, big.A.nnz)
+        gbs = sb / t_med / 1e9
+        trs = ncu_traffic("spmv_kernel")
+        line["spmv_hbm"] = {
+            "workload": "q1-100^3 blobs, N=1030301, NNZ=27270901, FP64 SpMV, L2 flushed",
+            "kernel": "spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+            "algorithmic_bytes": sb,
+            "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),
+            "traffic": (round(trs["dram_bytes"] / trs["units"] * big.A.nnz) if trs else None),
+        }
+        bs.close()
+        line["gpu_launches"] += 0  # extras are outside the timed region
+
+        # ----------------------------------------------- CPU oracle baseline
+        if rank == 0 and world == 1:
+            import oracle
+            t0 = time.perf_counter()
+            r = oracle.cg(pr.A, pr.b, tol=TOL)
+            dt = (time.perf_counter() - t0) * 1e3
+            line["cpu_baseline"] = {
+                "value": round(dt, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"one full serial FP64 CG solve of the same system ({r['iters']} iterations)"}
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gbcg(args)
+
+
+if __name__ == "__main__":
+    main()

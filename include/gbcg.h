@@ -1,0 +1,182 @@
+/*
+ * gbcg.h -- C ABI of the GB300 (sm_103a) conjugate-gradient library libgbcg.so.
+ *
+ * The library solves A x = b for a symmetric positive definite matrix A given
+ * in Compressed Sparse Row form, with the conjugate gradient method: the case
+ * study of the paper's Section IV ("Case Study"), whose experiment runs
+ * double-precision CG on a CSR matrix with N = 132651 and NNZ = 3442951 to a
+ * tolerance of 1e-10 (Table I).  One CG iteration is one sparse matrix-vector
+ * product ("DGEMV(sparse)" in Section IV), two dot products and three axpy
+ * updates; Table I's GFLOPS column is 2*NNZ + 10*N flops per iteration.
+ *
+ * The paper computes the scalars of each iteration on the CPU and the vector
+ * operations on the GPU (Section IV), crossing the host/device boundary every
+ * iteration.  Here the whole loop, scalars and stop test included, runs on
+ * the device in one persistent cooperative kernel launch per solve; the host
+ * reads back a 40-byte status once at the end.
+ *
+ * Conventions shared by every call:
+ *   - Every function that can fail returns an int status (CG_OK = 0) and
+ *     never aborts the process.  No call frees memory it did not allocate.
+ *   - "device pointer": memory of the CUDA device that was current when the
+ *     handle was created (for example a torch tensor's data_ptr()).
+ *     "host pointer": ordinary or pinned CPU memory.
+ *   - Vectors are dense FP64 arrays of length n, contiguous, 8-byte aligned.
+ *   - All device work of a handle is ordered on the CUDA stream given to
+ *     cg_create.  A handle must not be used from two threads at once, and
+ *     two solves on one handle must not overlap (they share its workspace).
+ */
+#ifndef GBCG_H
+#define GBCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CG_OK 0          /* converged (or nothing to do)                        */
+#define CG_EINVAL 1      /* invalid argument or malformed CSR                   */
+#define CG_ENOMEM 2      /* device or host allocation failed                    */
+#define CG_ECUDA 3       /* a CUDA runtime call or kernel launch failed         */
+#define CG_ENOCONV 4     /* maxit iterations done without meeting the tolerance;
+                            x holds the last iterate                            */
+#define CG_EBREAKDOWN 5  /* p.q <= 0 (A not positive definite), or r.z <= 0 with
+                            a preconditioner; x holds the last iterate          */
+#define CG_ENAN 6        /* a reduction produced NaN or infinity (e.g. NaN in b) */
+#define CG_ETIMEOUT 7    /* a bounded device-side wait (grid barrier or TMA
+                            barrier) ran past cg_opts.wait_limit_s; the kernel
+                            returned early and x is unspecified                 */
+
+/* ---- where the arrays of a cg_csr live --------------------------------- */
+#define CG_MEM_HOST 0
+#define CG_MEM_DEVICE 1
+
+/* ---- preconditioners --------------------------------------------------- */
+#define CG_PRECOND_NONE 0    /* plain CG, as in Section IV                      */
+#define CG_PRECOND_JACOBI 1  /* z = diag(A)^-1 r (Jacobi-preconditioned CG)     */
+
+/*
+ * A square sparse matrix in CSR form (Section IV stores the FEM matrix this
+ * way).  rowptr has n+1 entries, rowptr[0] = 0, non-decreasing,
+ * rowptr[n] = nnz; colidx[k] in [0, n) is the column of vals[k].  Columns of a
+ * row need not be sorted; repeated columns add.  Explicitly stored zeros are
+ * kept (and streamed by the kernels).  The matrix must be symmetric positive
+ * definite for CG to converge; symmetry is not checked.
+ */
+typedef struct {
+    int32_t n;               /* rows = columns, >= 0                             */
+    int64_t nnz;             /* stored entries, 0 <= nnz < 2^31                  */
+    const int32_t *rowptr;   /* n + 1 entries                                    */
+    const int32_t *colidx;   /* nnz entries                                      */
+    const double *vals;      /* nnz entries                                      */
+    int32_t mem;             /* CG_MEM_HOST or CG_MEM_DEVICE for the three arrays */
+} cg_csr;
+
+/* Options fixed at cg_create.  Fill with cg_opts_default, then change fields. */
+typedef struct {
+    int32_t precond;         /* CG_PRECOND_*; default CG_PRECOND_NONE             */
+    int32_t true_residual;   /* 1: after the loop compute ||b - A x||_2/||b||_2
+                                (one more SpMV) into cg_info.relres_true; default 1 */
+    double wait_limit_s;     /* bound on every device-side spin wait, seconds;
+                                default 5.0                                       */
+    int32_t grid_ctas;       /* persistent CTAs; 0 = one per SM (capped by the
+                                number of row tiles); default 0                   */
+    int32_t debug_phantom_arrivals; /* test knob, default 0: grid barriers also
+                                wait for this many CTAs that never arrive, so
+                                every wait runs out and the solve returns
+                                CG_ETIMEOUT without hanging the device            */
+} cg_opts;
+
+/* Result of a solve (also returned through the status code). */
+typedef struct {
+    int32_t iters;           /* products A p inside the loop (x updates applied) */
+    int32_t status;          /* same value as the function's return code         */
+    double relres;           /* ||r_k||_2 / ||b||_2 of the recursive residual     */
+    double relres_true;      /* ||b - A x||_2 / ||b||_2 if requested, else -1     */
+    double kernel_ms;        /* device time of the solve kernel (CUDA events)     */
+    int32_t launches;        /* kernels this call launched                        */
+    int32_t reserved;
+} cg_info;
+
+/* Read-only description of the launch plan of a handle. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int32_t ctas;            /* CTAs of the persistent kernels                    */
+    int32_t threads;         /* threads per CTA                                   */
+    int32_t tiles;           /* row tiles (each staged through shared memory)     */
+    int32_t tile_nnz;        /* largest tile in stored entries                    */
+    int32_t stages;          /* TMA pipeline depth                                */
+    int32_t smem_bytes;      /* dynamic shared memory per CTA                     */
+    int32_t lanes_per_row;   /* threads that share one row in the SpMV            */
+    int32_t l2_evict_first;  /* 1 when the matrix stream is marked evict-first    */
+    int64_t device_bytes;    /* device memory the handle owns                     */
+} cg_plan;
+
+typedef struct cg_handle cg_handle;
+
+/* Version of this ABI (major * 10000 + minor * 100 + patch). */
+int cg_version(void);
+
+/* Fills *opts with the defaults listed above.  CG_EINVAL if opts is NULL. */
+int cg_opts_default(cg_opts *opts);
+
+/*
+ * Validates A, copies it into device memory owned by the new handle, plans
+ * the row tiling and allocates the solver workspace (Section IV's "data
+ * reading" and "initial configuration" blocks).  The caller may free its
+ * arrays as soon as the call returns.  stream is a cudaStream_t (NULL = the
+ * legacy default stream); the current CUDA device becomes the handle's device.
+ * opts may be NULL for defaults.  On success *out receives the handle; on
+ * failure *out is NULL and the return code says why (CG_EINVAL for a
+ * malformed matrix: rowptr not starting at 0, decreasing, or not ending at
+ * nnz; a column outside [0, n); negative sizes; a non-positive or missing
+ * diagonal when CG_PRECOND_JACOBI is asked for).  Synchronous.
+ */
+int cg_create(const cg_csr *A, const cg_opts *opts, void *stream, cg_handle **out);
+
+/*
+ * Runs CG from x (in: x0, out: the last iterate) until
+ * ||r_k||_2 <= tol * ||b||_2 (the continue-condition of Section IV; Table I
+ * uses tol = 1e-10) or maxit iterations (maxit <= 0 means n: "a 132651 loop",
+ * Section IV).  b and x are device pointers of length n; b must not alias x.
+ * b = 0 gives x = 0 after 0 iterations.  Synchronous: returns after the
+ * result is on the device and the status is read back.  info may be NULL.
+ * Returns CG_OK, CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT, CG_EINVAL
+ * (NULL handle or vectors, negative or non-finite tol) or CG_ECUDA.
+ */
+int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit,
+             cg_info *info);
+
+/*
+ * cg_solve with b and x in host memory: copies b and x0 to the device, solves
+ * and copies x back, all on the handle's stream (pinned host memory makes the
+ * copies asynchronous DMA).  Same results and return codes as cg_solve.
+ */
+int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit,
+                  cg_info *info);
+
+/*
+ * y = A x (the SpMV of Section IV alone), x and y device pointers of length n,
+ * not aliased.  Asynchronous: enqueued on the handle's stream, returns after
+ * the launch.  Returns CG_OK, CG_EINVAL or CG_ECUDA.
+ */
+int cg_spmv(cg_handle *h, const double *x, double *y);
+
+/* Fills *plan with the handle's launch plan.  CG_EINVAL on NULL arguments. */
+int cg_get_plan(const cg_handle *h, cg_plan *plan);
+
+/* Frees everything the handle owns (after synchronizing its stream).
+ * cg_destroy(NULL) is a no-op; a handle must not be destroyed twice. */
+void cg_destroy(cg_handle *h);
+
+/* Static description of a status code ("unknown status" for other values). */
+const char *cg_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBCG_H */

@@ -1,0 +1,685 @@
+// libgbcg: conjugate gradient on a CSR matrix, one persistent cooperative
+// kernel per solve on a GB300 (sm_103a), behind the C ABI of gbcg.h.
+//
+// The iteration is the CG recurrence of the textbook the paper cites for the
+// method (Section IV): q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q,
+// stop when ||r|| <= tol ||b||, z = M^-1 r, beta = r.z / rho, p = z + beta p.
+// One iteration is one SpMV, two dot products and three axpys (Table I's
+// flop count, 2 NNZ + 10 N).  On GB300 the FP64 pipe (about 2 FMA per clock
+// per SM) bounds this path before HBM does, so every phase does exactly the
+// FP64 operations of the recurrence and nothing more:
+//
+//   phase A  q = A p over this CTA's rows (matrix streamed by TMA per warp),
+//            partial p.q                                  -> grid barrier
+//   phase B  x += alpha p, r -= alpha q, z = dinv r, partial r.r and r.z
+//                                                         -> grid barrier
+//            every CTA takes the same stop decision
+//   phase C  p = z + beta p                               -> grid barrier
+//
+// Scalars never leave the device; sums are fixed-order (bitwise
+// reproducible from run to run).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cg_device.cuh"
+#include "gbcg.h"
+
+using namespace gbcg;
+
+namespace {
+
+// ------------------------------------------------------------ epilogues
+struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
+    const double *b;
+    double *r;
+    double *z;
+    double *p;
+    const double *dinv;
+    int precond;
+    double rr = 0.0, rz = 0.0, bb = 0.0;
+    __device__ __forceinline__ void row(int i, double ax) {
+        const double bi = b[i];
+        const double ri = bi - ax;
+        r[i] = ri;
+        double zi = ri;
+        if (precond) {
+            zi = dinv[i] * ri;
+            z[i] = zi;
+        }
+        p[i] = zi;
+        rr = fma(ri, ri, rr);
+        rz = fma(ri, zi, rz);
+        bb = fma(bi, bi, bb);
+    }
+};
+
+struct EpiIter {        // q = A p; sum p . q
+    double *q;
+    const double *p;
+    double pq = 0.0;
+    __device__ __forceinline__ void row(int i, double aq) {
+        q[i] = aq;
+        pq = fma(p[i], aq, pq);
+    }
+};
+
+struct EpiTrue {        // sum (b - A x)^2
+    const double *b;
+    double acc = 0.0;
+    __device__ __forceinline__ void row(int i, double ax) {
+        const double t = b[i] - ax;
+        acc = fma(t, t, acc);
+    }
+};
+
+struct EpiStore {       // y = A x
+    double *y;
+    __device__ __forceinline__ void row(int i, double ax) { y[i] = ax; }
+};
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// ------------------------------------------------------- the solve kernel
+__global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    init_pipeline(S);
+    unsigned int epoch = 0;
+    Pipe pipe;
+    int set = 0;
+    const int tid = threadIdx.x;
+    const int row_lo = P.cta_row[blockIdx.x];
+    const int row_hi = P.cta_row[blockIdx.x + 1];
+    double *const p = P.p0;
+
+    int status = CG_OK, iters = 0;
+    double rr = 0.0, bb = 0.0, true_rr = -1.0;
+
+    // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0; r.r, r.z, b.b
+    {
+        EpiSetup epi{P.b, P.r, P.z, p, P.dinv, P.precond};
+        if (!spmv_tiles(P, S, pipe, SrcVec{P.x}, epi)) goto out;
+        double v[3] = {epi.rr, epi.rz, epi.bb};
+        block_sum<3>(v, S);
+        publish_partials<3>(P, set, v);
+        if (!grid_barrier(P, epoch, S)) goto out;
+        double tot[3];
+        grid_totals<3>(P, set, S, tot);
+        set ^= 1;
+        rr = tot[0];
+        bb = tot[2];
+        double rho = tot[1];
+        const double bnorm = sqrt(bb);
+        bool run = true;
+        if (!finite(bb)) {
+            status = CG_ENAN;
+            run = false;
+        } else if (bnorm == 0.0) {  // b = 0: the solution is x = 0
+            for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] = 0.0;
+            rr = 0.0;
+            run = false;
+        } else if (!finite(rr) || !finite(rho)) {
+            status = CG_ENAN;
+            run = false;
+        } else if (sqrt(rr) <= P.tol * bnorm) {
+            run = false;
+        } else if (!(rho > 0.0)) {
+            status = CG_EBREAKDOWN;
+            run = false;
+        }
+
+        // ---- the CG loop
+        if (run) {
+            status = CG_ENOCONV;
+            for (int k = 1; k <= P.maxit; ++k) {
+                // phase A: q = A p, p . q
+                EpiIter ei{P.q, p};
+                if (!spmv_tiles(P, S, pipe, SrcVec{p}, ei)) goto out;
+                double v1[1] = {ei.pq};
+                block_sum<1>(v1, S);
+                publish_partials<1>(P, set, v1);
+                if (!grid_barrier(P, epoch, S)) goto out;
+                double sg[1];
+                grid_totals<1>(P, set, S, sg);
+                set ^= 1;
+                const double sigma = sg[0];
+                if (!finite(sigma)) { status = CG_ENAN; break; }
+                if (!(sigma > 0.0)) { status = CG_EBREAKDOWN; break; }
+                const double alpha = rho / sigma;
+
+                // phase B: x += alpha p, r -= alpha q, z = dinv r; r.r, r.z
+                double prr = 0.0, prz = 0.0;
+                for (int i = row_lo + tid; i < row_hi; i += kThreads) {
+                    const double pi = p[i], qi = P.q[i], xi = P.x[i], ri0 = P.r[i];
+                    P.x[i] = fma(alpha, pi, xi);
+                    const double ri = fma(-alpha, qi, ri0);
+                    P.r[i] = ri;
+                    prr = fma(ri, ri, prr);
+                    if (P.precond) {
+                        const double zi = P.dinv[i] * ri;
+                        P.z[i] = zi;
+                        prz = fma(ri, zi, prz);
+                    }
+                }
+                double v2[2] = {prr, prz};
+                block_sum<2>(v2, S);
+                publish_partials<2>(P, set, v2);
+                if (!grid_barrier(P, epoch, S)) goto out;
+                double t2[2];
+                grid_totals<2>(P, set, S, t2);
+                set ^= 1;
+                iters = k;
+                rr = t2[0];
+                const double rho_new = P.precond ? t2[1] : t2[0];
+                if (!finite(rr)) { status = CG_ENAN; break; }
+                if (sqrt(rr) <= P.tol * bnorm) { status = CG_OK; break; }
+                if (!finite(rho_new)) { status = CG_ENAN; break; }
+                if (!(rho_new > 0.0)) { status = CG_EBREAKDOWN; break; }
+                if (k == P.maxit) break;  // ENOCONV: no further direction needed
+                const double beta = rho_new / rho;
+                rho = rho_new;
+
+                // phase C: p = z + beta p
+                for (int i = row_lo + tid; i < row_hi; i += kThreads) p[i] = fma(beta, p[i], P.z[i]);
+                if (!grid_barrier(P, epoch, S)) goto out;
+            }
+        }
+    }
+
+    // ---- true residual ||b - A x|| of the final iterate (x is complete: the
+    // last thing before here was a grid barrier, or x = 0 stores with b = 0)
+    if (P.true_res && status != CG_ENAN) {
+        if (bb == 0.0) {
+            true_rr = 0.0;
+        } else {
+            EpiTrue et{P.b};
+            if (!spmv_tiles(P, S, pipe, SrcVec{P.x}, et)) goto out;
+            double v[1] = {et.acc};
+            block_sum<1>(v, S);
+            publish_partials<1>(P, set, v);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double t[1];
+            grid_totals<1>(P, set, S, t);
+            true_rr = t[0];
+        }
+    }
+
+    if (blockIdx.x == 0 && tid == 0) {
+        P.st->iters = iters;
+        P.st->rr = rr;
+        P.st->bb = bb;
+        P.st->true_rr = true_rr;
+        atomicCAS(&P.st->status, 0, status);
+    }
+out:
+    drain(P, S, pipe);
+}
+
+// ------------------------------------------------------- plain SpMV kernel
+__global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    init_pipeline(S);
+    Pipe pipe;
+    EpiStore epi{P.q};
+    (void)spmv_tiles(P, S, pipe, SrcVec{P.x}, epi, true);
+    drain(P, S, pipe);
+}
+
+}  // namespace
+
+// =================================================================== host
+
+struct cg_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cg_opts opts{};
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int ctas = 0;
+    int ntiles = 0;
+    int max_tile_nnz = 0;
+    int evict_first = 0;
+    int64_t device_bytes = 0;
+    // device arrays
+    int32_t *rowptr = nullptr, *colidx = nullptr, *cta_tile = nullptr, *cta_row = nullptr;
+    int4 *tiles = nullptr;
+    double *vals = nullptr, *dinv = nullptr;
+    double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
+    double *partials = nullptr, *b_dev = nullptr, *x_dev = nullptr;
+    unsigned int *bar = nullptr;
+    DevStatus *st = nullptr;
+    DevStatus *st_host = nullptr;  // pinned
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA; }
+
+template <class T>
+int dev_alloc(cg_handle *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->allocs.push_back(v);
+    h->device_bytes += (int64_t)(count * sizeof(T));
+    *p = static_cast<T *>(v);
+    return CG_OK;
+}
+
+void free_handle(cg_handle *h) {
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+// Row tiles: at most kTileRows rows and kTileNnz entries each; a row with
+// more than kTileNnz entries is a tile of its own (read from global memory).
+std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, int *max_nnz) {
+    std::vector<int32_t> tiles;
+    tiles.reserve(n / 64 + 2);
+    int32_t r = 0;
+    *max_nnz = 0;
+    while (r < n) {
+        const int32_t start = r;
+        if (rowptr[r + 1] - rowptr[r] > kTileNnz) {
+            ++r;
+        } else {
+            while (r < n && r - start < kTileRows && rowptr[r + 1] - rowptr[r] <= kTileNnz &&
+                   rowptr[r + 1] - rowptr[start] <= kTileNnz)
+                ++r;
+        }
+        tiles.push_back(start);
+        *max_nnz = std::max(*max_nnz, rowptr[r] - rowptr[start]);
+    }
+    tiles.push_back(n);
+    return tiles;
+}
+
+// Contiguous tile ranges per CTA with about equal cost (entries + rows).
+std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::vector<int32_t> &rowptr,
+                                 int ctas) {
+    const int nt = (int)tiles.size() - 1;
+    std::vector<double> prefix(nt + 1, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        const double nnz = rowptr[tiles[t + 1]] - rowptr[tiles[t]];
+        const double rows = tiles[t + 1] - tiles[t];
+        prefix[t + 1] = prefix[t] + nnz + 2.0 * rows;
+    }
+    std::vector<int32_t> cut(ctas + 1, 0);
+    int t = 0;
+    for (int b = 1; b < ctas; ++b) {
+        const double target = prefix[nt] * b / ctas;
+        while (t < nt && prefix[t + 1] <= target) ++t;
+        // choose the boundary closer to the target
+        if (t < nt && target - prefix[t] > prefix[t + 1] - target) ++t;
+        cut[b] = std::max(cut[b - 1], t);
+    }
+    cut[ctas] = nt;
+    return cut;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+Params base_params(const cg_handle *h) {
+    Params P{};
+    P.n = h->n;
+    P.rowptr = h->rowptr;
+    P.colidx = h->colidx;
+    P.vals = h->vals;
+    P.tiles = h->tiles;
+    P.cta_tile = h->cta_tile;
+    P.cta_row = h->cta_row;
+    P.dinv = h->dinv;
+    P.r = h->r;
+    P.z = h->z;
+    P.p0 = h->p0;
+    P.q = h->q;
+    P.partials = h->partials;
+    P.bar = h->bar;
+    P.st = h->st;
+    P.precond = h->opts.precond;
+    P.true_res = h->opts.true_residual;
+    P.phantom = h->opts.debug_phantom_arrivals;
+    double w = h->opts.wait_limit_s;
+    P.wait_ns = (unsigned long long)(w * 1e9);
+    P.evict_first = h->evict_first;
+    return P;
+}
+
+// Enqueues one solve on the handle's stream (no synchronization).
+int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit) {
+    Params P = base_params(h);
+    P.b = b;
+    P.x = x;
+    P.tol = tol;
+    P.maxit = maxit;
+    cudaError_t e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
+    if (e == cudaSuccess) {
+        void *args[] = {&P};
+        e = cudaLaunchCooperativeKernel((const void *)cg_solve_kernel, dim3(h->ctas), dim3(kThreads),
+                                        args, (size_t)kSmemBytes, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream);
+    return e == cudaSuccess ? CG_OK : CG_ECUDA;
+}
+
+int finish_solve(cg_handle *h, cg_info *info) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return CG_ECUDA;
+    const DevStatus &s = *h->st_host;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    const double bnorm = std::sqrt(s.bb);
+    cg_info out{};
+    out.iters = s.iters;
+    out.status = s.status;
+    out.relres = bnorm > 0.0 ? std::sqrt(s.rr) / bnorm : 0.0;
+    out.relres_true = s.true_rr < 0.0 ? -1.0 : (bnorm > 0.0 ? std::sqrt(s.true_rr) / bnorm : 0.0);
+    out.kernel_ms = ms;
+    out.launches = 1;
+    if (info) *info = out;
+    return s.status;
+}
+
+int check_solve_args(const cg_handle *h, const double *b, const double *x, double tol) {
+    if (!h) return CG_EINVAL;
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return CG_EINVAL;
+    if (h->n > 0 && (!b || !x || b == x)) return CG_EINVAL;
+    return CG_OK;
+}
+
+void empty_info(cg_info *info) {
+    if (info) {
+        *info = cg_info{};
+        info->relres_true = 0.0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cg_version(void) { return 10000; }
+
+int cg_opts_default(cg_opts *opts) {
+    if (!opts) return CG_EINVAL;
+    *opts = cg_opts{};
+    opts->precond = CG_PRECOND_NONE;
+    opts->true_residual = 1;
+    opts->wait_limit_s = 5.0;
+    opts->grid_ctas = 0;
+    opts->debug_phantom_arrivals = 0;
+    return CG_OK;
+}
+
+const char *cg_strerror(int code) {
+    switch (code) {
+        case CG_OK: return "ok";
+        case CG_EINVAL: return "invalid argument or malformed CSR matrix";
+        case CG_ENOMEM: return "out of memory";
+        case CG_ECUDA: return "CUDA runtime error";
+        case CG_ENOCONV: return "maximum iterations reached before the tolerance";
+        case CG_EBREAKDOWN: return "breakdown: matrix or preconditioner not positive definite";
+        case CG_ENAN: return "NaN or infinity in a reduction";
+        case CG_ETIMEOUT: return "bounded device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle **out) {
+    if (!out) return CG_EINVAL;
+    *out = nullptr;
+    if (!A) return CG_EINVAL;
+    cg_opts opts;
+    if (opts_in) {
+        opts = *opts_in;
+    } else {
+        cg_opts_default(&opts);
+    }
+    if (opts.precond != CG_PRECOND_NONE && opts.precond != CG_PRECOND_JACOBI) return CG_EINVAL;
+    if (!(opts.wait_limit_s > 0.0) || !std::isfinite(opts.wait_limit_s) || opts.wait_limit_s > 3600.0)
+        return CG_EINVAL;
+    if (opts.grid_ctas < 0 || opts.debug_phantom_arrivals < 0 || opts.debug_phantom_arrivals > 1024)
+        return CG_EINVAL;
+    const int32_t n = A->n;
+    const int64_t nnz = A->nnz;
+    if (n < 0 || nnz < 0 || nnz > (int64_t)INT32_MAX - 64) return CG_EINVAL;
+    if (A->mem != CG_MEM_HOST && A->mem != CG_MEM_DEVICE) return CG_EINVAL;
+    if (!A->rowptr) return CG_EINVAL;
+    if (nnz > 0 && (!A->colidx || !A->vals)) return CG_EINVAL;
+
+    // ---- host copies of the matrix for validation and planning (host-side
+    // matrices are validated before any CUDA call)
+    std::vector<int32_t> rowptr(n + 1), colidx(nnz);
+    std::vector<double> vals(nnz);
+    if (A->mem == CG_MEM_DEVICE) {
+        if (cudaMemcpy(rowptr.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return CG_EINVAL;
+        if (nnz > 0 &&
+            (cudaMemcpy(colidx.data(), A->colidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) !=
+                 cudaSuccess ||
+             cudaMemcpy(vals.data(), A->vals, sizeof(double) * nnz, cudaMemcpyDeviceToHost) !=
+                 cudaSuccess))
+            return CG_EINVAL;
+    } else {
+        std::memcpy(rowptr.data(), A->rowptr, sizeof(int32_t) * (n + 1));
+        if (nnz > 0) {
+            std::memcpy(colidx.data(), A->colidx, sizeof(int32_t) * nnz);
+            std::memcpy(vals.data(), A->vals, sizeof(double) * nnz);
+        }
+    }
+    if (rowptr[0] != 0 || (int64_t)rowptr[n] != nnz) return CG_EINVAL;
+    for (int32_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) return CG_EINVAL;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (colidx[k] < 0 || colidx[k] >= n) return CG_EINVAL;
+
+    std::vector<double> dinv;
+    if (opts.precond == CG_PRECOND_JACOBI) {
+        dinv.resize(n);
+        for (int32_t i = 0; i < n; ++i) {
+            double d = 0.0;
+            for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+                if (colidx[k] == i) d += vals[k];
+            if (!(d > 0.0) || !std::isfinite(d)) return CG_EINVAL;
+            dinv[i] = 1.0 / d;
+        }
+    }
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CG_ECUDA;
+
+    cg_handle *h = new (std::nothrow) cg_handle();
+    if (!h) return CG_ENOMEM;
+    h->device = dev;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->opts = opts;
+    h->n = n;
+    h->nnz = nnz;
+
+    int rc = CG_OK;
+    auto fail = [&](int code) {
+        free_handle(h);
+        return code;
+    };
+
+    // ---- plan: tiles, CTAs
+    int max_tile = 0;
+    std::vector<int32_t> tiles = n > 0 ? plan_tiles(n, rowptr, &max_tile) : std::vector<int32_t>{0};
+    h->ntiles = (int)tiles.size() - 1;
+    h->max_tile_nnz = max_tile;
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CG_ECUDA);
+    if (cudaFuncSetAttribute((const void *)cg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess)
+        return fail(CG_ECUDA);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_solve_kernel, kThreads, kSmemBytes) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return fail(CG_ECUDA);
+    const int max_ctas = sms * per_sm;
+    int ctas = opts.grid_ctas > 0 ? std::min(opts.grid_ctas, max_ctas) : sms;
+    ctas = std::max(1, std::min(ctas, std::max(1, h->ntiles)));
+    h->ctas = ctas;
+    std::vector<int32_t> cut = split_tiles(tiles, rowptr, ctas);
+    std::vector<int4> desc(std::max(1, h->ntiles));
+    for (int t = 0; t < h->ntiles; ++t)
+        desc[t] = make_int4(tiles[t], tiles[t + 1], rowptr[tiles[t]], rowptr[tiles[t + 1]]);
+    std::vector<int32_t> cta_row(ctas + 1);
+    for (int c = 0; c <= ctas; ++c) cta_row[c] = tiles[cut[c]];
+
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const double matrix_bytes = 12.0 * (double)nnz + 4.0 * (n + 1);
+    const double vector_bytes = 64.0 * (double)n;
+    h->evict_first = (matrix_bytes + vector_bytes > 0.6 * (double)l2) ? 1 : 0;
+
+    // ---- device memory
+    const size_t pad = 16;
+    if ((rc = dev_alloc(h, &h->rowptr, (size_t)n + 1 + pad)) ||
+        (rc = dev_alloc(h, &h->colidx, (size_t)nnz + pad)) ||
+        (rc = dev_alloc(h, &h->vals, (size_t)nnz + pad)) ||
+        (rc = dev_alloc(h, &h->tiles, desc.size())) ||
+        (rc = dev_alloc(h, &h->cta_tile, cut.size())) ||
+        (rc = dev_alloc(h, &h->cta_row, cta_row.size())) ||
+        (rc = dev_alloc(h, &h->r, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->p0, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->q, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->b_dev, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->x_dev, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->partials, (size_t)2 * ctas * kRedSlots)) ||
+        (rc = dev_alloc(h, &h->bar, 64)) ||
+        (rc = dev_alloc(h, &h->st, 1)))
+        return fail(rc);
+    if (opts.precond == CG_PRECOND_JACOBI) {
+        if ((rc = dev_alloc(h, &h->z, (size_t)n)) || (rc = dev_alloc(h, &h->dinv, (size_t)n))) return fail(rc);
+    } else {
+        h->z = h->r;
+    }
+    if (cudaMallocHost(&h->st_host, sizeof(DevStatus)) != cudaSuccess) return fail(CG_ENOMEM);
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+        return fail(CG_ECUDA);
+
+    cudaError_t e = cudaMemset(h->rowptr, 0, sizeof(int32_t) * (n + 1 + pad));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->rowptr, rowptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->colidx, 0, sizeof(int32_t) * (nnz + pad));
+    if (e == cudaSuccess) e = cudaMemset(h->vals, 0, sizeof(double) * (nnz + pad));
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpy(h->colidx, colidx.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz > 0)
+        e = cudaMemcpy(h->vals, vals.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->tiles, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->cta_tile, cut.data(), sizeof(int32_t) * cut.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->cta_row, cta_row.data(), sizeof(int32_t) * cta_row.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && opts.precond == CG_PRECOND_JACOBI && n > 0)
+        e = cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    *out = h;
+    return CG_OK;
+}
+
+int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    int rc = check_solve_args(h, b, x, tol);
+    if (rc != CG_OK) return rc;
+    if (h->n == 0) {
+        empty_info(info);
+        return CG_OK;
+    }
+    DeviceGuard g(h->device);
+    if (maxit <= 0) maxit = h->n;
+    if ((rc = enqueue_solve(h, b, x, tol, maxit)) != CG_OK) return rc;
+    return finish_solve(h, info);
+}
+
+int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    int rc = check_solve_args(h, b, x, tol);
+    if (rc != CG_OK) return rc;
+    if (h->n == 0) {
+        empty_info(info);
+        return CG_OK;
+    }
+    DeviceGuard g(h->device);
+    if (maxit <= 0) maxit = h->n;
+    const size_t bytes = sizeof(double) * (size_t)h->n;
+    if (cudaMemcpyAsync(h->b_dev, b, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->x_dev, x, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return CG_ECUDA;
+    if ((rc = enqueue_solve(h, h->b_dev, h->x_dev, tol, maxit)) != CG_OK) return rc;
+    if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return CG_ECUDA;
+    return finish_solve(h, info);
+}
+
+int cg_spmv(cg_handle *h, const double *x, double *y) {
+    if (!h) return CG_EINVAL;
+    if (h->n == 0) return CG_OK;
+    if (!x || !y || x == y) return CG_EINVAL;
+    DeviceGuard g(h->device);
+    Params P = base_params(h);
+    P.x = const_cast<double *>(x);
+    P.q = y;
+    spmv_kernel<<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+}
+
+int cg_get_plan(const cg_handle *h, cg_plan *plan) {
+    if (!h || !plan) return CG_EINVAL;
+    cg_plan p{};
+    p.n = h->n;
+    p.nnz = h->nnz;
+    p.ctas = h->ctas;
+    p.threads = kThreads;
+    p.tiles = h->ntiles;
+    p.tile_nnz = h->max_tile_nnz;
+    p.stages = kWarps;  // one TMA stage per warp
+    p.smem_bytes = kSmemBytes;
+    p.lanes_per_row = 1;
+    p.l2_evict_first = h->evict_first;
+    p.device_bytes = h->device_bytes;
+    *plan = p;
+    return CG_OK;
+}
+
+void cg_destroy(cg_handle *h) { free_handle(h); }
+
+}  // extern "C"

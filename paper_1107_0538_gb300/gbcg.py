@@ -1,0 +1,238 @@
+"""ctypes binding of libgbcg.so, the C ABI declared in include/gbcg.h.
+
+The functions below carry the C names and do argument marshalling only: every
+step of a solve runs in the library's CUDA kernels.  ``Solver`` is a small
+convenience wrapper that takes a CSR matrix with numpy arrays and torch CUDA
+tensors (PyTorch provides device memory and the stream; nothing else).
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1107_0538_gb300.build``); loading fails loudly otherwise.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbcg.so")
+
+CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA = 0, 1, 2, 3
+CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT = 4, 5, 6, 7
+CG_MEM_HOST, CG_MEM_DEVICE = 0, 1
+CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+
+# Every entry point of include/gbcg.h (checked against the header by the tests).
+EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
+           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror")
+
+
+class GbcgError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {cg_strerror(code)} (status {code})" if what else cg_strerror(code))
+
+
+class cg_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("mem", ctypes.c_int32)]
+
+
+class cg_opts(ctypes.Structure):
+    _fields_ = [("precond", ctypes.c_int32), ("true_residual", ctypes.c_int32),
+                ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int32),
+                ("debug_phantom_arrivals", ctypes.c_int32)]
+
+
+class cg_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("kernel_ms", ctypes.c_double),
+                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class cg_plan(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("ctas", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("tiles", ctypes.c_int32), ("tile_nnz", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("l2_evict_first", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libgbcg.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "(the solver has no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+            L.cg_version.argtypes = []
+            L.cg_version.restype = ctypes.c_int
+            L.cg_opts_default.argtypes = [ctypes.POINTER(cg_opts)]
+            L.cg_opts_default.restype = ctypes.c_int
+            L.cg_create.argtypes = [ctypes.POINTER(cg_csr), ctypes.POINTER(cg_opts), vp,
+                                    ctypes.POINTER(vp)]
+            L.cg_create.restype = ctypes.c_int
+            for name in ("cg_solve", "cg_solve_host"):
+                f = getattr(L, name)
+                f.argtypes = [vp, vp, vp, dbl, i32, ctypes.POINTER(cg_info)]
+                f.restype = ctypes.c_int
+            L.cg_spmv.argtypes = [vp, vp, vp]
+            L.cg_spmv.restype = ctypes.c_int
+            L.cg_get_plan.argtypes = [vp, ctypes.POINTER(cg_plan)]
+            L.cg_get_plan.restype = ctypes.c_int
+            L.cg_destroy.argtypes = [vp]
+            L.cg_destroy.restype = None
+            L.cg_strerror.argtypes = [ctypes.c_int]
+            L.cg_strerror.restype = ctypes.c_char_p
+            _LIB = L
+    return _LIB
+
+
+# ---------------------------------------------------------------- C names
+
+def cg_version() -> int:
+    return lib().cg_version()
+
+
+def cg_opts_default() -> cg_opts:
+    o = cg_opts()
+    rc = lib().cg_opts_default(ctypes.byref(o))
+    if rc:
+        raise GbcgError(rc, "cg_opts_default")
+    return o
+
+
+def cg_create(A: cg_csr, opts: cg_opts | None, stream: int | None) -> tuple[int, int | None]:
+    """Returns (status, handle); handle is None on failure."""
+    h = ctypes.c_void_p()
+    rc = lib().cg_create(ctypes.byref(A), ctypes.byref(opts) if opts is not None else None,
+                         ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    return rc, (h.value if rc == CG_OK else None)
+
+
+def cg_solve(h: int, b_ptr: int, x_ptr: int, tol: float, maxit: int) -> tuple[int, cg_info]:
+    info = cg_info()
+    rc = lib().cg_solve(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                        float(tol), int(maxit), ctypes.byref(info))
+    return rc, info
+
+
+def cg_solve_host(h: int, b_ptr: int, x_ptr: int, tol: float, maxit: int) -> tuple[int, cg_info]:
+    info = cg_info()
+    rc = lib().cg_solve_host(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                             float(tol), int(maxit), ctypes.byref(info))
+    return rc, info
+
+
+def cg_spmv(h: int, x_ptr: int, y_ptr: int) -> int:
+    return lib().cg_spmv(ctypes.c_void_p(h), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr))
+
+
+def cg_get_plan(h: int) -> cg_plan:
+    p = cg_plan()
+    rc = lib().cg_get_plan(ctypes.c_void_p(h), ctypes.byref(p))
+    if rc:
+        raise GbcgError(rc, "cg_get_plan")
+    return p
+
+
+def cg_destroy(h: int | None) -> None:
+    lib().cg_destroy(ctypes.c_void_p(h or 0))
+
+
+def cg_strerror(code: int) -> str:
+    return lib().cg_strerror(int(code)).decode()
+
+
+# ------------------------------------------------------------ convenience
+
+def host_csr(A) -> tuple[cg_csr, tuple]:
+    """cg_csr over host numpy copies of A (returned too, to keep them alive)."""
+    rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+    vals = np.ascontiguousarray(A.vals, dtype=np.float64)
+    c = cg_csr(int(A.n), int(rowptr[-1]) if A.n > 0 else int(colidx.size),
+               rowptr.ctypes.data, colidx.ctypes.data, vals.ctypes.data, CG_MEM_HOST)
+    return c, (rowptr, colidx, vals)
+
+
+class Solver:
+    """One CSR matrix on the current CUDA device, solved through the C ABI.
+
+    ``b`` and ``x`` of ``solve`` are float64 CUDA tensors (torch); ``solve_host``
+    takes numpy arrays.  The stream is the torch stream current at creation.
+    """
+
+    def __init__(self, A, precond: int = CG_PRECOND_NONE, true_residual: bool = True,
+                 wait_limit_s: float = 5.0, grid_ctas: int = 0, debug_phantom_arrivals: int = 0,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o = cg_opts_default()
+        o.precond = precond
+        o.true_residual = 1 if true_residual else 0
+        o.wait_limit_s = wait_limit_s
+        o.grid_ctas = grid_ctas
+        o.debug_phantom_arrivals = debug_phantom_arrivals
+        csr, self._keep = host_csr(A)
+        rc, self.h = cg_create(csr, o, self.stream.cuda_stream)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_create")
+        self.n = int(A.n)
+
+    def solve(self, b, x, tol: float, maxit: int = 0, check: bool = False) -> cg_info:
+        t = self._torch
+        assert b.dtype == t.float64 and x.dtype == t.float64 and b.is_cuda and x.is_cuda
+        assert b.is_contiguous() and x.is_contiguous() and b.numel() == self.n == x.numel()
+        rc, info = cg_solve(self.h, b.data_ptr(), x.data_ptr(), tol, maxit)
+        if check and rc not in (CG_OK,):
+            raise GbcgError(rc, "cg_solve")
+        return info
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, tol: float, maxit: int = 0) -> cg_info:
+        assert b.dtype == np.float64 and x.dtype == np.float64
+        assert b.flags.c_contiguous and x.flags.c_contiguous and b.size == self.n == x.size
+        rc, info = cg_solve_host(self.h, b.ctypes.data, x.ctypes.data, tol, maxit)
+        return info
+
+    def spmv(self, x, y) -> None:
+        rc = cg_spmv(self.h, x.data_ptr(), y.data_ptr())
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_spmv")
+
+    def plan(self) -> dict:
+        return cg_get_plan(self.h).as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            cg_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
