@@ -87,6 +87,10 @@ typedef struct {
                                 wait for this many CTAs that never arrive, so
                                 every wait runs out and the solve returns
                                 CG_ETIMEOUT without hanging the device            */
+    int32_t vectors_in_memory; /* 0 (default): when every thread owns at most 4
+                                rows, the solver keeps x, r, z, p, q and 1/diag of
+                                those rows in registers for the whole solve;
+                                1: always keep every vector in device memory     */
 } cg_opts;
 
 /* Result of a solve (also returned through the status code). */
@@ -108,10 +112,12 @@ typedef struct {
     int32_t threads;         /* threads per CTA                                   */
     int32_t tiles;           /* row tiles (each staged through shared memory)     */
     int32_t tile_nnz;        /* largest tile in stored entries                    */
-    int32_t stages;          /* TMA pipeline depth                                */
+    int32_t stages;          /* TMA stages (shared-memory tile buffers) per CTA   */
     int32_t smem_bytes;      /* dynamic shared memory per CTA                     */
     int32_t lanes_per_row;   /* threads that share one row in the SpMV            */
     int32_t l2_evict_first;  /* 1 when the matrix stream is marked evict-first    */
+    int32_t reg_rows;        /* rows per thread held in registers (0: none)       */
+    int32_t window_tiles;    /* tiles whose gathers read a staged x-window        */
     int64_t device_bytes;    /* device memory the handle owns                     */
 } cg_plan;
 

@@ -15,7 +15,8 @@ import sys
 _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", "gbcg.cu")]
-DEPS = SOURCES + [os.path.join(_HERE, "csrc", "cg_device.cuh"), os.path.join(ROOT, "include", "gbcg.h")]
+DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("cg_device.cuh", "layout.h", "plan.h")] + [
+    os.path.join(ROOT, "include", "gbcg.h")]
 OUT = os.path.join(_HERE, "libgbcg.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -8,36 +8,9 @@
 #include <cuda_runtime.h>
 
 #include "gbcg.h"
+#include "layout.h"
 
 namespace gbcg {
-
-// ---------------------------------------------------------------- geometry
-// FP64 arithmetic is the scarce resource on GB300 (about 2 FP64 FMA per clock
-// per SM, 56x below FP32), so the SpMV gives every row to one thread: exactly
-// one FMA per stored entry, no cross-lane reduction adds, no padded slots.
-// Each warp streams its own tiles of up to 32 rows through its own shared
-// memory stage with TMA bulk copies and its own mbarrier, so warps never
-// wait for each other inside the SpMV.
-constexpr int kThreads = 512;                  // threads per CTA
-constexpr int kWarps = kThreads / 32;
-constexpr int kTileRows = 32;                  // rows per warp tile (one per lane)
-constexpr int kTileNnz = 1024;                 // stored entries per warp tile
-constexpr int kBatch = 9;                      // gathers in flight per thread
-constexpr int kValsStage = kTileNnz + 8;       // doubles per stage (alignment slack)
-constexpr int kColsStage = kTileNnz + 8;       // int32 per stage
-constexpr int kRptrStage = kTileRows + 8;      // int32 per stage (row pointers)
-constexpr int kStageBytes = kValsStage * 8 + kColsStage * 4 + kRptrStage * 4;
-constexpr int kRedSlots = 4;                   // partial sums per CTA per barrier
-constexpr int kSmemBytes = kWarps * kStageBytes + kWarps * 8 /*mbarriers*/ +
-                           kWarps * kRedSlots * 8 + 64 /*broadcast*/;
-static_assert(kStageBytes % 16 == 0, "stage alignment");
-static_assert(kTileNnz + 6 <= kColsStage && kTileNnz + 2 <= kValsStage, "stage slack");
-static_assert(kTileRows + 1 + 6 <= kRptrStage, "row pointer slack");
-
-// One row tile: rows [r0, r1) holding entries [a, e).
-struct TileDesc {
-    int32_t r0, r1, a, e;
-};
 
 // Device status block read back once per solve.
 struct DevStatus {
@@ -56,7 +29,10 @@ struct Params {
     const int32_t *__restrict__ rowptr;
     const int32_t *__restrict__ colidx;   // padded to a multiple of 4 + slack
     const double *__restrict__ vals;      // padded to a multiple of 2 + slack
-    const int4 *__restrict__ tiles;       // ntiles descriptors (TileDesc)
+    const int4 *__restrict__ tiles;       // 2 x ntiles int4 (TileDesc)
+    const uint16_t *__restrict__ lcol;    // local column of each entry (windowed tiles)
+    const int4 *__restrict__ segs;        // window segments: {first column (even), window offset,
+                                          //  doubles copied by TMA, tail column or -1}
     const int32_t *__restrict__ cta_tile; // gridDim.x + 1 tile boundaries
     const int32_t *__restrict__ cta_row;  // gridDim.x + 1 row boundaries
     const double *__restrict__ dinv;      // Jacobi: 1 / diag(A), else nullptr
@@ -179,9 +155,9 @@ __device__ __forceinline__ void set_error(DevStatus *st, int code, int where) {
 struct Smem {
     unsigned char *stage;   // kWarps x kStageBytes (one stage per warp)
     uint64_t *mbar;         // kWarps
-    double *red;            // kWarps x kRedSlots
-    double *bcast;          // 4 doubles
-    int *flag;              // 1 int
+    double *red;            // kThreads doubles: block-sum transpose
+    double *bcast;          // 8 doubles: scalars broadcast by thread 0
+    int *ctl;               // 16 ints: decisions broadcast by thread 0
     __device__ __forceinline__ double *vals(int s) const {
         return reinterpret_cast<double *>(stage + s * kStageBytes);
     }
@@ -191,6 +167,10 @@ struct Smem {
     __device__ __forceinline__ int32_t *rptr(int s) const {
         return reinterpret_cast<int32_t *>(stage + s * kStageBytes + kValsStage * 8 + kColsStage * 4);
     }
+    __device__ __forceinline__ double *win(int s) const {
+        return reinterpret_cast<double *>(stage + s * kStageBytes + kValsStage * 8 + kColsStage * 4 +
+                                          kRptrStage * 4);
+    }
 };
 
 __device__ __forceinline__ Smem carve_smem(unsigned char *base) {
@@ -198,8 +178,8 @@ __device__ __forceinline__ Smem carve_smem(unsigned char *base) {
     S.stage = base;
     S.mbar = reinterpret_cast<uint64_t *>(base + kWarps * kStageBytes);
     S.red = reinterpret_cast<double *>(base + kWarps * kStageBytes + kWarps * 8);
-    S.bcast = S.red + kWarps * kRedSlots;
-    S.flag = reinterpret_cast<int *>(S.bcast + 4);
+    S.bcast = S.red + kThreads;
+    S.ctl = reinterpret_cast<int *>(S.bcast + 8);
     return S;
 }
 
@@ -212,26 +192,27 @@ __device__ __forceinline__ void init_pipeline(const Smem &S) {
 }
 
 // ---------------------------------------------- deterministic reductions
-// Sums NV per-thread values over the CTA in a fixed order; thread 0 returns
-// the totals (other threads get unspecified values).
+// A warp-wide FP64 instruction costs the same FP64-pipe time however many of
+// its lanes are active, so the sums below keep FP64 work to one warp: every
+// thread parks its value in shared memory (no FP64 op) and warp 0 adds the
+// kThreads values (kThreads / 32 adds per lane in a fixed order, then a
+// 5-level butterfly).  Thread 0 returns the totals; the order is the same in
+// every CTA and every run.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], const Smem &S) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
-    if (lane == 0) {
+    for (int j = 0; j < NV; ++j) {
+        S.red[threadIdx.x] = v[j];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double t = S.red[lane];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) S.red[warp * kRedSlots + j] = v[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            double t = lane < kWarps ? S.red[lane * kRedSlots + j] : 0.0;
+            for (int m = 1; m < kWarps; ++m) t += S.red[lane + 32 * m];
             v[j] = warp_sum(t);
         }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // Writes this CTA's partial sums (held by thread 0) for barrier set `set`.
@@ -244,11 +225,10 @@ __device__ __forceinline__ void publish_partials(const Params &P, int set, const
     }
 }
 
-// Sums the partials of every CTA for barrier set `set` in a fixed order; all
-// threads of all CTAs obtain bitwise-identical totals.
+// Sums the partials of every CTA for barrier set `set` in a fixed order
+// (warp 0 only); thread 0 gets the totals, bitwise identical in every CTA.
 template <int NV>
-__device__ __forceinline__ void grid_totals(const Params &P, int set, const Smem &S,
-                                            double (&out)[NV]) {
+__device__ __forceinline__ void grid_totals(const Params &P, int set, double (&out)[NV]) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
         const double *src = P.partials + (size_t)set * gridDim.x * kRedSlots;
@@ -266,13 +246,14 @@ __device__ __forceinline__ void grid_totals(const Params &P, int set, const Smem
 #pragma unroll
                 for (int u = 0; u < 8; ++u) s += v[u];
             }
-            s = warp_sum(s);
-            if (lane == 0) S.bcast[j] = s;
+            out[j] = warp_sum(s);
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NV; ++j) out[j] = S.bcast[j];
+}
+
+// IEEE finiteness from the exponent bits (integer ops, not the FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
 }
 
 // Grid-wide barrier on a monotonically increasing counter: barrier number
@@ -300,126 +281,212 @@ __device__ __forceinline__ bool grid_barrier(const Params &P, unsigned int &epoc
         }
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (!ok) set_error(P.st, CG_ETIMEOUT, 1);
-        S.flag[0] = ok;
+        S.ctl[15] = ok;
     }
     __syncthreads();
-    return S.flag[0] != 0;
+    return S.ctl[15] != 0;
 }
 
 // ------------------------------------------------------------ tiled SpMV
-// Sources of the vector the SpMV multiplies.
-struct SrcVec {   // v_j = x_j
-    const double *x;
-    __device__ __forceinline__ double operator()(int j) const { return x[j]; }
-};
-
 __device__ __forceinline__ TileDesc load_desc(const Params &P, int t) {
-    const int4 d = __ldg(P.tiles + t);
-    return TileDesc{d.x, d.y, d.z, d.w};
+    const int4 d0 = __ldg(P.tiles + 2 * t), d1 = __ldg(P.tiles + 2 * t + 1);
+    return TileDesc{d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 }
 
 // Per-warp TMA pipeline.  Warp w of a CTA owns the CTA's tiles w, w + kWarps,
 // w + 2 kWarps, ... (m of them per pass).  Its running count c over all
-// passes maps to local tile w + kWarps (c mod m); the warp's single stage
-// completes mbarrier phase c mod 2 for count c.  The matrix never changes, so
-// after consuming its last tile of a pass the warp already issues its first
-// tile of the next pass: that copy overlaps the vector phase and the grid
-// barriers.
+// passes maps to local tile w + kWarps (c mod m) and completes phase c mod 2
+// of the warp's mbarrier.  The matrix part of a tile (values, columns, row
+// pointers) never changes, so the warp issues it one tile ahead, across
+// passes too: the first tile of the next SpMV loads while the vector phases
+// and grid barriers run.  The x-window part can only be issued once the
+// multiplied vector is final, i.e. inside the pass that uses it; the
+// mbarrier expects both parts from the start.
 struct Pipe {
     uint32_t consumed = 0;
-    uint32_t issued = 0;
+    uint32_t issued = 0;      // tiles whose matrix part is issued
+    uint32_t win_issued = 0;  // tiles whose window part is issued
 };
 
-// Issues the TMA copies of tile t into this warp's stage (lane 0 only):
-// values, column indices and the row pointers rowptr[r0 .. r1].
-__device__ __forceinline__ void issue_tile(const Params &P, const Smem &S, int t, int w) {
-    const TileDesc d = load_desc(P, t);
-    if (d.e - d.a > kTileNnz) {  // long row: read straight from global memory
-        mbar_arrive(&S.mbar[w]);
+// Matrix part of tile t into stage s (lane 0).
+__device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, const TileDesc &d, int s) {
+    if (d.kind == kTileLong) {
+        mbar_arrive(&S.mbar[s]);
         return;
     }
-    const int va = d.a & ~1, ve = (d.e + 1) & ~1;              // 16-byte aligned ranges
-    const int ca = d.a & ~3, ce = (d.e + 3) & ~3;
+    const int va = d.a & ~1, ve = (d.e + 1) & ~1;   // 16-byte aligned ranges
     const int ra = d.r0 & ~3, re = (d.r1 + 1 + 3) & ~3;
-    const uint32_t vbytes = (uint32_t)(ve - va) * 8u, cbytes = (uint32_t)(ce - ca) * 4u;
-    const uint32_t rbytes = (uint32_t)(re - ra) * 4u;
-    mbar_arrive_expect_tx(&S.mbar[w], vbytes + cbytes + rbytes);
-    if (vbytes) {
-        tma_load_1d(S.vals(w), P.vals + va, vbytes, &S.mbar[w], P.evict_first != 0);
-        tma_load_1d(S.cols(w), P.colidx + ca, cbytes, &S.mbar[w], P.evict_first != 0);
+    const uint32_t vbytes = (uint32_t)(ve - va) * 8u, rbytes = (uint32_t)(re - ra) * 4u;
+    uint32_t cbytes;
+    const void *csrc;
+    if (d.kind == kTileWindow) {
+        const int ca = d.a & ~7, ce = (d.e + 7) & ~7;
+        cbytes = (uint32_t)(ce - ca) * 2u;
+        csrc = P.lcol + ca;
+    } else {
+        const int ca = d.a & ~3, ce = (d.e + 3) & ~3;
+        cbytes = (uint32_t)(ce - ca) * 4u;
+        csrc = P.colidx + ca;
     }
-    tma_load_1d(S.rptr(w), P.rowptr + ra, rbytes, &S.mbar[w], false);
+    // the window bytes the TMA will deliver (a tail column, if any, is stored
+    // by a thread instead)
+    const uint32_t wbytes = (uint32_t)d.wtx * 8u;
+    mbar_arrive_expect_tx(&S.mbar[s], (d.e > d.a ? vbytes + cbytes : 0u) + rbytes + wbytes);
+    if (d.e > d.a) {
+        tma_load_1d(S.vals(s), P.vals + va, vbytes, &S.mbar[s], P.evict_first != 0);
+        tma_load_1d(S.cols(s), csrc, cbytes, &S.mbar[s], P.evict_first != 0);
+    }
+    tma_load_1d(S.rptr(s), P.rowptr + ra, rbytes, &S.mbar[s], false);
 }
 
-// Row sums of this CTA's rows: epi.row(i, sum_k vals[k] * src(colidx[k])) is
-// called once per row by one thread.  `limit` caps the running count of
-// issued tiles per warp (the plain SpMV kernel allows one pass; the solver
-// lets each warp run one tile ahead and drains at the end).  Returns false in
-// every thread of the CTA if a TMA wait ran out (the error is recorded).
-template <class Src, class Epi>
-__device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe &pp,
-                                           const Src &src, Epi &epi, bool one_pass = false) {
+// Window part of a windowed tile into stage s: lane l copies segment l of
+// the vector x (16-byte aligned).
+__device__ __forceinline__ void issue_window(const Params &P, const Smem &S, const TileDesc &d, int s,
+                                             const double *x) {
+    const int lane = threadIdx.x & 31;
+    if (d.kind != kTileWindow || lane >= d.nseg) return;
+    const int4 sg = __ldg(P.segs + d.seg0 + lane);
+    if (sg.z > 0) tma_load_1d(S.win(s) + sg.y, x + sg.x, (uint32_t)sg.z * 8u, &S.mbar[s], false);
+}
+
+// A segment ending on the vector's last column when n is odd would run one
+// element past the vector; its TMA copy stops short and its lane stores that
+// column into the window slot after the copied part.
+__device__ __forceinline__ void store_tail(const Params &P, const Smem &S, const TileDesc &d, int s,
+                                           const double *x) {
+    const int lane = threadIdx.x & 31;
+    if (d.kind != kTileWindow || lane >= d.nseg) return;
+    const int4 sg = __ldg(P.segs + d.seg0 + lane);
+    if (sg.w >= 0) S.win(s)[sg.y + sg.z] = x[sg.w];
+}
+
+__device__ __forceinline__ void issue_next(const Params &P, const Smem &S, Pipe &pp, int t0, int m,
+                                           uint32_t limit, uint32_t pass_end, const double *x) {
+    const int w = threadIdx.x >> 5;
+    if (pp.issued < pp.consumed + 1 && pp.issued < limit) {
+        const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.issued % (uint32_t)m));
+        // order this warp's generic shared-memory writes to the stage (tail
+        // columns) before the async-proxy copies that will overwrite it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) issue_matrix(P, S, d, w);
+        __syncwarp();
+        if (pp.issued < pass_end) {  // same pass: the vector is final, load the window now
+            issue_window(P, S, d, w, x);
+            ++pp.win_issued;
+        }
+        ++pp.issued;
+    }
+}
+
+// Sum over one row: exactly one FMA per stored entry, the loads of a batch
+// issued before its first FMA, two interleaved accumulators.
+template <class Col, class Val>
+__device__ __forceinline__ double row_sum(int k0, int k1, const Col &col_of, const Val &val_of,
+                                          const double *vs) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int kb = k0; kb < k1; kb += kBatch) {
+        double v[kBatch], xv[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = min(kb + u, k1 - 1);  // clamped: every load is in range
+            v[u] = vs[k];
+            xv[u] = val_of(col_of(k));
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (kb + u < k1) {
+                if (u & 1) s1 = fma(v[u], xv[u], s1);
+                else s0 = fma(v[u], xv[u], s0);
+            }
+        }
+    }
+    return s0 + s1;
+}
+
+// One tile of a warp: waits for its stage, forms the row sums and calls
+// epi.row(i, sum, j) for each row i of the tile (lane l gets row r0 + l; j is
+// the warp's local tile number in the pass).  Returns false if the wait ran
+// out.
+template <class Epi>
+__device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &pp, int t0, int m,
+                                          uint32_t limit, uint32_t pass_end, const double *x, Epi &epi,
+                                          int j) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t c = pp.consumed;
+    const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(c % (uint32_t)m));
+    store_tail(P, S, d, w, x);  // nobody reads the stage before the wait below
+    const bool got = mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns);
+    if (__any_sync(0xffffffffu, !got)) return false;
+    __syncwarp();
+    if (d.kind == kTileLong) {
+        // one long row: the warp reduces it straight from global memory
+        double part = 0.0;
+        for (int k = d.a + lane; k < d.e; k += 32) part = fma(P.vals[k], x[P.colidx[k]], part);
+        part = warp_sum(part);
+        if (lane == 0) epi.row(d.r0, part, j);
+    } else {
+        const double *vs = S.vals(w) - (d.a & ~1);
+        const int32_t *rs = S.rptr(w) - (d.r0 & ~3);
+        const int row = d.r0 + lane;
+        if (row < d.r1) {
+            const int k0 = rs[row], k1 = rs[row + 1];
+            double sum = 0.0;
+            if (k1 > k0) {
+                if (d.kind == kTileWindow) {
+                    const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols(w)) - (d.a & ~7);
+                    const double *win = S.win(w);
+                    sum = row_sum(k0, k1, [&](int k) { return (int)lc[k]; },
+                                  [&](int c2) { return win[c2]; }, vs);
+                } else {
+                    const int32_t *cs = S.cols(w) - (d.a & ~3);
+                    sum = row_sum(k0, k1, [&](int k) { return cs[k]; },
+                                  [&](int c2) { return x[c2]; }, vs);
+                }
+            }
+            epi.row(row, sum, j);
+        }
+    }
+    __syncwarp();  // every lane is done with the stage
+    ++pp.consumed;
+    issue_next(P, S, pp, t0, m, limit, pass_end, x);
+    return true;
+}
+
+// Row sums of this CTA's rows with the vector x (16-byte aligned, padded):
+// epi.row(i, sum_k vals[k] * x[colidx[k]], j) is called once per row by the
+// thread that owns it.  RPT > 0 unrolls the warp's tile loop (at most RPT
+// tiles per warp) so that j is a compile-time index into register-resident
+// row state; RPT = 0 loops at run time.  `one_pass` stops the pipeline at the
+// end of the pass (the plain SpMV); otherwise the next pass's first tile is
+// left in flight (matrix part only).  Returns false in every thread of the
+// CTA if a TMA wait ran out (the error is recorded).
+template <int RPT, class Epi>
+__device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe &pp, const double *x,
+                                           Epi &epi, bool one_pass = false) {
     const int t0 = P.cta_tile[blockIdx.x], t1 = P.cta_tile[blockIdx.x + 1];
     const int nt = t1 - t0;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int m = nt > w ? (nt - w + kWarps - 1) / kWarps : 0;   // this warp's tiles per pass
     bool failed = false;
     if (m > 0) {
-        const uint32_t limit = one_pass ? (uint32_t)m : 0xffffffffu;
-        if (pp.issued == pp.consumed && pp.issued < limit) {   // nothing in flight yet
-            if (lane == 0) issue_tile(P, S, t0 + w, w);
-            ++pp.issued;
+        const uint32_t pass_end = pp.consumed + (uint32_t)m;
+        const uint32_t limit = one_pass ? pass_end : 0xffffffffu;
+        // windows of tiles whose matrix part was issued during the last pass
+        while (pp.win_issued < pp.issued) {
+            const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
+            issue_window(P, S, d, w, x);
+            ++pp.win_issued;
         }
-        for (int j = 0; j < m; ++j) {
-            const uint32_t c = pp.consumed;
-            const int t = t0 + w + kWarps * (int)(c % (uint32_t)m);
-            const TileDesc d = load_desc(P, t);
-            const bool got = mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns);
-            if (__any_sync(0xffffffffu, !got)) {
-                failed = true;
-                break;
-            }
-            if (d.e - d.a > kTileNnz) {
-                // one long row: the warp reduces it straight from global memory
-                double part = 0.0;
-                for (int k = d.a + lane; k < d.e; k += 32) part = fma(P.vals[k], src(P.colidx[k]), part);
-                part = warp_sum(part);
-                if (lane == 0) epi.row(d.r0, part);
-            } else {
-                const double *vs = S.vals(w) - (d.a & ~1);
-                const int32_t *cs = S.cols(w) - (d.a & ~3);
-                const int32_t *rs = S.rptr(w) - (d.r0 & ~3);
-                const int row = d.r0 + lane;
-                if (row < d.r1) {
-                    const int k0 = rs[row], k1 = rs[row + 1];
-                    // two interleaved accumulators halve the dependent FMA chain
-                    double s0 = 0.0, s1 = 0.0;
-                    for (int kb = k0; kb < k1; kb += kBatch) {
-                        double v[kBatch], xv[kBatch];
+        issue_next(P, S, pp, t0, m, limit, pass_end, x);
+        if (RPT > 0) {
 #pragma unroll
-                        for (int u = 0; u < kBatch; ++u) {
-                            const int k = kb + u;
-                            const int col = k < k1 ? cs[k] : -1;
-                            v[u] = k < k1 ? vs[k] : 0.0;
-                            xv[u] = col >= 0 ? src(col) : 0.0;
-                        }
-#pragma unroll
-                        for (int u = 0; u < kBatch; ++u) {
-                            if (kb + u < k1) {
-                                if (u & 1) s1 = fma(v[u], xv[u], s1);
-                                else s0 = fma(v[u], xv[u], s0);
-                            }
-                        }
-                    }
-                    epi.row(row, s0 + s1);
-                }
+            for (int j = 0; j < (RPT > 0 ? RPT : 1); ++j) {
+                if (j < m && !failed) failed = !warp_tile(P, S, pp, t0, m, limit, pass_end, x, epi, j);
             }
-            __syncwarp();  // every lane is done with the stage
-            ++pp.consumed;
-            if (pp.issued < limit) {
-                if (lane == 0) issue_tile(P, S, t0 + w + kWarps * (int)(pp.issued % (uint32_t)m), w);
-                ++pp.issued;
-            }
+        } else {
+            for (int j = 0; j < m && !failed; ++j)
+                failed = !warp_tile(P, S, pp, t0, m, limit, pass_end, x, epi, j);
         }
     }
     if (__syncthreads_or(failed)) {
@@ -430,14 +497,25 @@ __device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe 
 }
 
 // Waits (bounded) for every tile still in flight, so that no TMA copy
-// targets shared memory after the CTA exits.
-__device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp) {
+// targets shared memory after the CTA exits.  A prefetched tile whose window
+// was never issued cannot complete its phase, so the window is issued first
+// (from any vector: the data is not used).
+__device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp, const double *any_x) {
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        for (uint32_t c = pp.consumed; c < pp.issued; ++c) {
-            if (!mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns)) {
-                set_error(P.st, CG_ETIMEOUT, 3);
-                break;
+    const int t0 = P.cta_tile[blockIdx.x], nt = P.cta_tile[blockIdx.x + 1] - t0;
+    const int m = nt > w ? (nt - w + kWarps - 1) / kWarps : 0;
+    if (m > 0) {
+        while (pp.win_issued < pp.issued) {
+            const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
+            issue_window(P, S, d, w, any_x);
+            ++pp.win_issued;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            for (uint32_t c = pp.consumed; c < pp.issued; ++c) {
+                if (!mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns)) {
+                    set_error(P.st, CG_ETIMEOUT, 3);
+                    break;
+                }
             }
         }
     }

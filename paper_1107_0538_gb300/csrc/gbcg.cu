@@ -29,11 +29,27 @@
 #include <vector>
 
 #include "cg_device.cuh"
+#include "plan.h"
 #include "gbcg.h"
 
 using namespace gbcg;
 
+static_assert(sizeof(I4) == sizeof(int4), "tile descriptor layout");
+
 namespace {
+
+// ------------------------------------------------------------ row state
+// With RPT > 0 every thread keeps the vector entries of the rows it owns
+// (lane l of warp w owns row r0 + l of each of the warp's tiles) in
+// registers for the whole solve: x, r, z, p, q and 1/diag never round-trip
+// through memory; only p is published (the SpMV gathers it) and x is written
+// at the end.  RPT = 0 keeps every vector in global memory.
+template <int RPT>
+struct RegRows {
+    int row[RPT > 0 ? RPT : 1];
+    double x[RPT > 0 ? RPT : 1], r[RPT > 0 ? RPT : 1], z[RPT > 0 ? RPT : 1];
+    double p[RPT > 0 ? RPT : 1], q[RPT > 0 ? RPT : 1], dinv[RPT > 0 ? RPT : 1];
+};
 
 // ------------------------------------------------------------ epilogues
 struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
@@ -44,7 +60,7 @@ struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
     const double *dinv;
     int precond;
     double rr = 0.0, rz = 0.0, bb = 0.0;
-    __device__ __forceinline__ void row(int i, double ax) {
+    __device__ __forceinline__ void row(int i, double ax, int) {
         const double bi = b[i];
         const double ri = bi - ax;
         r[i] = ri;
@@ -60,20 +76,51 @@ struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
     }
 };
 
+template <int RPT>
+struct RegSetup {       // the same, into registers (p is also published)
+    RegRows<RPT> &R;
+    const double *b;
+    double *p;
+    int precond;
+    double rr = 0.0, rz = 0.0, bb = 0.0;
+    __device__ __forceinline__ void row(int i, double ax, int j) {
+        const double bi = b[i];
+        const double ri = bi - ax;
+        const double zi = precond ? R.dinv[j] * ri : ri;
+        R.r[j] = ri;
+        R.z[j] = zi;
+        R.p[j] = zi;
+        p[i] = zi;
+        rr = fma(ri, ri, rr);
+        rz = fma(ri, zi, rz);
+        bb = fma(bi, bi, bb);
+    }
+};
+
 struct EpiIter {        // q = A p; sum p . q
     double *q;
     const double *p;
     double pq = 0.0;
-    __device__ __forceinline__ void row(int i, double aq) {
+    __device__ __forceinline__ void row(int i, double aq, int) {
         q[i] = aq;
         pq = fma(p[i], aq, pq);
+    }
+};
+
+template <int RPT>
+struct RegIter {
+    RegRows<RPT> &R;
+    double pq = 0.0;
+    __device__ __forceinline__ void row(int, double aq, int j) {
+        R.q[j] = aq;
+        pq = fma(R.p[j], aq, pq);
     }
 };
 
 struct EpiTrue {        // sum (b - A x)^2
     const double *b;
     double acc = 0.0;
-    __device__ __forceinline__ void row(int i, double ax) {
+    __device__ __forceinline__ void row(int i, double ax, int) {
         const double t = b[i] - ax;
         acc = fma(t, t, acc);
     }
@@ -81,12 +128,21 @@ struct EpiTrue {        // sum (b - A x)^2
 
 struct EpiStore {       // y = A x
     double *y;
-    __device__ __forceinline__ void row(int i, double ax) { y[i] = ax; }
+    __device__ __forceinline__ void row(int i, double ax, int) { y[i] = ax; }
 };
 
-__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+// Decisions thread 0 takes from the reduced scalars and broadcasts.
+// Each slot is rewritten only after a __syncthreads that follows every read
+// of its previous value.
+constexpr int kCtlRun = 0;       // 1: continue iterating
+constexpr int kCtlZeroB = 2;     // 1: b = 0, so x = 0
+constexpr int kCtlTrue = 3;      // 1: compute the true residual
 
 // ------------------------------------------------------- the solve kernel
+// Scalar recurrences (alpha, beta, the stop test) run in thread 0 only: on
+// GB300 an FP64 divide or square root executed by every warp would cost the
+// FP64 pipe as much as a tile of the SpMV.
+template <int RPT>
 __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Smem S = carve_smem(smem_raw);
@@ -99,63 +155,140 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
     const int row_hi = P.cta_row[blockIdx.x + 1];
     double *const p = P.p0;
 
+    // thread 0's scalar state
     int status = CG_OK, iters = 0;
-    double rr = 0.0, bb = 0.0, true_rr = -1.0;
+    double rr = 0.0, bb = 0.0, true_rr = -1.0, rho = 0.0, bnorm = 0.0;
+    RegRows<RPT> R;
+    if constexpr (RPT > 0) {
+        const int t0 = P.cta_tile[blockIdx.x], nt = P.cta_tile[blockIdx.x + 1] - t0;
+        const int w = tid >> 5, lane = tid & 31;
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            R.row[j] = -1;
+            R.x[j] = 0.0;
+            R.dinv[j] = 1.0;
+            const int t = w + kWarps * j;
+            if (t < nt) {
+                const TileDesc d = load_desc(P, t0 + t);
+                const int row = d.r0 + lane;
+                if (row < d.r1) {
+                    R.row[j] = row;
+                    R.x[j] = P.x[row];
+                    if (P.precond) R.dinv[j] = P.dinv[row];
+                }
+            }
+        }
+    }
 
     // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0; r.r, r.z, b.b
+    bool run;
     {
-        EpiSetup epi{P.b, P.r, P.z, p, P.dinv, P.precond};
-        if (!spmv_tiles(P, S, pipe, SrcVec{P.x}, epi)) goto out;
-        double v[3] = {epi.rr, epi.rz, epi.bb};
+        double v[3];
+        if constexpr (RPT > 0) {
+            RegSetup<RPT> epi{R, P.b, p, P.precond};
+            if (!spmv_tiles<RPT>(P, S, pipe, P.x, epi)) goto out;
+            v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
+        } else {
+            EpiSetup epi{P.b, P.r, P.z, p, P.dinv, P.precond};
+            if (!spmv_tiles<0>(P, S, pipe, P.x, epi)) goto out;
+            v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
+        }
         block_sum<3>(v, S);
         publish_partials<3>(P, set, v);
         if (!grid_barrier(P, epoch, S)) goto out;
         double tot[3];
-        grid_totals<3>(P, set, S, tot);
+        grid_totals<3>(P, set, tot);
         set ^= 1;
-        rr = tot[0];
-        bb = tot[2];
-        double rho = tot[1];
-        const double bnorm = sqrt(bb);
-        bool run = true;
-        if (!finite(bb)) {
-            status = CG_ENAN;
-            run = false;
-        } else if (bnorm == 0.0) {  // b = 0: the solution is x = 0
-            for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] = 0.0;
-            rr = 0.0;
-            run = false;
-        } else if (!finite(rr) || !finite(rho)) {
-            status = CG_ENAN;
-            run = false;
-        } else if (sqrt(rr) <= P.tol * bnorm) {
-            run = false;
-        } else if (!(rho > 0.0)) {
-            status = CG_EBREAKDOWN;
-            run = false;
+        if (tid == 0) {
+            rr = tot[0];
+            bb = tot[2];
+            rho = tot[1];
+            bnorm = sqrt(bb);
+            int go = 0, zero_b = 0;
+            if (!finite_bits(bb)) {
+                status = CG_ENAN;
+            } else if (bnorm == 0.0) {
+                rr = 0.0;
+                zero_b = 1;
+            } else if (!finite_bits(rr) || !finite_bits(rho)) {
+                status = CG_ENAN;
+            } else if (sqrt(rr) <= P.tol * bnorm) {
+                status = CG_OK;
+            } else if (!(rho > 0.0)) {
+                status = CG_EBREAKDOWN;
+            } else {
+                go = 1;
+            }
+            S.ctl[kCtlRun] = go;
+            S.ctl[kCtlZeroB] = zero_b;
         }
+        __syncthreads();
+        run = S.ctl[kCtlRun] != 0;
+        if (S.ctl[kCtlZeroB]) {  // b = 0: the solution is x = 0
+            if constexpr (RPT > 0) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) R.x[j] = 0.0;
+            } else {
+                for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] = 0.0;
+            }
+        }
+    }
 
-        // ---- the CG loop
-        if (run) {
-            status = CG_ENOCONV;
-            for (int k = 1; k <= P.maxit; ++k) {
-                // phase A: q = A p, p . q
+    // ---- the CG loop
+    if (run) {
+        if (tid == 0) status = CG_ENOCONV;
+        for (int k = 1; k <= P.maxit; ++k) {
+            // phase A: q = A p, p . q
+            double pq;
+            if constexpr (RPT > 0) {
+                RegIter<RPT> ei{R};
+                if (!spmv_tiles<RPT>(P, S, pipe, p, ei)) goto out;
+                pq = ei.pq;
+            } else {
                 EpiIter ei{P.q, p};
-                if (!spmv_tiles(P, S, pipe, SrcVec{p}, ei)) goto out;
-                double v1[1] = {ei.pq};
-                block_sum<1>(v1, S);
-                publish_partials<1>(P, set, v1);
-                if (!grid_barrier(P, epoch, S)) goto out;
-                double sg[1];
-                grid_totals<1>(P, set, S, sg);
-                set ^= 1;
+                if (!spmv_tiles<0>(P, S, pipe, p, ei)) goto out;
+                pq = ei.pq;
+            }
+            double v1[1] = {pq};
+            block_sum<1>(v1, S);
+            publish_partials<1>(P, set, v1);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double sg[1];
+            grid_totals<1>(P, set, sg);
+            set ^= 1;
+            if (tid == 0) {
                 const double sigma = sg[0];
-                if (!finite(sigma)) { status = CG_ENAN; break; }
-                if (!(sigma > 0.0)) { status = CG_EBREAKDOWN; break; }
-                const double alpha = rho / sigma;
+                int go = 0;
+                if (!finite_bits(sigma)) status = CG_ENAN;
+                else if (!(sigma > 0.0)) status = CG_EBREAKDOWN;
+                else go = 1;
+                S.bcast[0] = go ? rho / sigma : 0.0;
+                S.ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!S.ctl[kCtlRun]) break;
+            const double alpha = S.bcast[0];
 
-                // phase B: x += alpha p, r -= alpha q, z = dinv r; r.r, r.z
-                double prr = 0.0, prz = 0.0;
+            // phase B: x += alpha p, r -= alpha q, z = dinv r; r.r, r.z
+            double prr = 0.0, prz = 0.0;
+            if constexpr (RPT > 0) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    if (R.row[j] >= 0) {
+                        R.x[j] = fma(alpha, R.p[j], R.x[j]);
+                        const double ri = fma(-alpha, R.q[j], R.r[j]);
+                        R.r[j] = ri;
+                        prr = fma(ri, ri, prr);
+                        if (P.precond) {
+                            const double zi = R.dinv[j] * ri;
+                            R.z[j] = zi;
+                            prz = fma(ri, zi, prz);
+                        } else {
+                            R.z[j] = ri;
+                        }
+                    }
+                }
+            } else {
                 for (int i = row_lo + tid; i < row_hi; i += kThreads) {
                     const double pi = p[i], qi = P.q[i], xi = P.x[i], ri0 = P.r[i];
                     P.x[i] = fma(alpha, pi, xi);
@@ -168,46 +301,85 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
                         prz = fma(ri, zi, prz);
                     }
                 }
+            }
+            double t2[2];
+            if (P.precond) {
                 double v2[2] = {prr, prz};
                 block_sum<2>(v2, S);
                 publish_partials<2>(P, set, v2);
                 if (!grid_barrier(P, epoch, S)) goto out;
-                double t2[2];
-                grid_totals<2>(P, set, S, t2);
-                set ^= 1;
+                grid_totals<2>(P, set, t2);
+            } else {
+                double v2[1] = {prr};
+                block_sum<1>(v2, S);
+                publish_partials<1>(P, set, v2);
+                if (!grid_barrier(P, epoch, S)) goto out;
+                double t1[1];
+                grid_totals<1>(P, set, t1);
+                t2[0] = t1[0];
+                t2[1] = t1[0];
+            }
+            set ^= 1;
+            if (tid == 0) {
                 iters = k;
                 rr = t2[0];
-                const double rho_new = P.precond ? t2[1] : t2[0];
-                if (!finite(rr)) { status = CG_ENAN; break; }
-                if (sqrt(rr) <= P.tol * bnorm) { status = CG_OK; break; }
-                if (!finite(rho_new)) { status = CG_ENAN; break; }
-                if (!(rho_new > 0.0)) { status = CG_EBREAKDOWN; break; }
-                if (k == P.maxit) break;  // ENOCONV: no further direction needed
-                const double beta = rho_new / rho;
-                rho = rho_new;
-
-                // phase C: p = z + beta p
-                for (int i = row_lo + tid; i < row_hi; i += kThreads) p[i] = fma(beta, p[i], P.z[i]);
-                if (!grid_barrier(P, epoch, S)) goto out;
+                const double rho_new = t2[1];
+                int go = 0;
+                if (!finite_bits(rr)) status = CG_ENAN;
+                else if (sqrt(rr) <= P.tol * bnorm) status = CG_OK;
+                else if (!finite_bits(rho_new)) status = CG_ENAN;
+                else if (!(rho_new > 0.0)) status = CG_EBREAKDOWN;
+                else if (k < P.maxit) go = 1;  // else ENOCONV: no further direction needed
+                if (go) {
+                    S.bcast[1] = rho_new / rho;
+                    rho = rho_new;
+                }
+                S.ctl[kCtlRun] = go;
             }
+            __syncthreads();
+            if (!S.ctl[kCtlRun]) break;
+            const double beta = S.bcast[1];
+
+            // phase C: p = z + beta p
+            if constexpr (RPT > 0) {
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    if (R.row[j] >= 0) {
+                        R.p[j] = fma(beta, R.p[j], R.z[j]);
+                        p[R.row[j]] = R.p[j];
+                    }
+                }
+            } else {
+                for (int i = row_lo + tid; i < row_hi; i += kThreads) p[i] = fma(beta, p[i], P.z[i]);
+            }
+            if (!grid_barrier(P, epoch, S)) goto out;
         }
     }
 
-    // ---- true residual ||b - A x|| of the final iterate (x is complete: the
-    // last thing before here was a grid barrier, or x = 0 stores with b = 0)
-    if (P.true_res && status != CG_ENAN) {
-        if (bb == 0.0) {
-            true_rr = 0.0;
-        } else {
+    // ---- publish x (register mode), then the true residual ||b - A x||
+    if constexpr (RPT > 0) {
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+            if (R.row[j] >= 0) P.x[R.row[j]] = R.x[j];
+    }
+    {
+        if (tid == 0) S.ctl[kCtlTrue] = (P.true_res && status != CG_ENAN && bb != 0.0) ? 1 : 0;
+        __syncthreads();
+        const bool want_true = S.ctl[kCtlTrue] != 0;
+        if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
+        if (want_true) {
+            if constexpr (RPT > 0) {
+                if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
+            }
             EpiTrue et{P.b};
-            if (!spmv_tiles(P, S, pipe, SrcVec{P.x}, et)) goto out;
+            if (!spmv_tiles<RPT>(P, S, pipe, P.x, et)) goto out;
             double v[1] = {et.acc};
             block_sum<1>(v, S);
             publish_partials<1>(P, set, v);
             if (!grid_barrier(P, epoch, S)) goto out;
             double t[1];
-            grid_totals<1>(P, set, S, t);
-            true_rr = t[0];
+            grid_totals<1>(P, set, t);
+            if (tid == 0) true_rr = t[0];
         }
     }
 
@@ -219,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
         atomicCAS(&P.st->status, 0, status);
     }
 out:
-    drain(P, S, pipe);
+    drain(P, S, pipe, p);
 }
 
 // ------------------------------------------------------- plain SpMV kernel
@@ -229,8 +401,19 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
     init_pipeline(S);
     Pipe pipe;
     EpiStore epi{P.q};
-    (void)spmv_tiles(P, S, pipe, SrcVec{P.x}, epi, true);
-    drain(P, S, pipe);
+    (void)spmv_tiles<0>(P, S, pipe, P.x, epi, true);
+    drain(P, S, pipe, P.x);
+}
+
+using SolveKernel = void (*)(Params);
+constexpr int kRptChoices[] = {0, 1, 2, 4};
+SolveKernel solve_kernel_for(int rpt) {
+    switch (rpt) {
+        case 1: return cg_solve_kernel<1>;
+        case 2: return cg_solve_kernel<2>;
+        case 4: return cg_solve_kernel<4>;
+        default: return cg_solve_kernel<0>;
+    }
 }
 
 }  // namespace
@@ -245,12 +428,16 @@ struct cg_handle {
     int64_t nnz = 0;
     int ctas = 0;
     int ntiles = 0;
+    int rpt = 0;                      // rows per thread kept in registers (0: none)
+    SolveKernel kernel = nullptr;
     int max_tile_nnz = 0;
     int evict_first = 0;
     int64_t device_bytes = 0;
     // device arrays
     int32_t *rowptr = nullptr, *colidx = nullptr, *cta_tile = nullptr, *cta_row = nullptr;
-    int4 *tiles = nullptr;
+    int4 *tiles = nullptr, *segs = nullptr;
+    uint16_t *lcol = nullptr;
+    int window_tiles = 0;
     double *vals = nullptr, *dinv = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
     double *partials = nullptr, *b_dev = nullptr, *x_dev = nullptr;
@@ -292,52 +479,6 @@ void free_handle(cg_handle *h) {
     delete h;
 }
 
-// Row tiles: at most kTileRows rows and kTileNnz entries each; a row with
-// more than kTileNnz entries is a tile of its own (read from global memory).
-std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, int *max_nnz) {
-    std::vector<int32_t> tiles;
-    tiles.reserve(n / 64 + 2);
-    int32_t r = 0;
-    *max_nnz = 0;
-    while (r < n) {
-        const int32_t start = r;
-        if (rowptr[r + 1] - rowptr[r] > kTileNnz) {
-            ++r;
-        } else {
-            while (r < n && r - start < kTileRows && rowptr[r + 1] - rowptr[r] <= kTileNnz &&
-                   rowptr[r + 1] - rowptr[start] <= kTileNnz)
-                ++r;
-        }
-        tiles.push_back(start);
-        *max_nnz = std::max(*max_nnz, rowptr[r] - rowptr[start]);
-    }
-    tiles.push_back(n);
-    return tiles;
-}
-
-// Contiguous tile ranges per CTA with about equal cost (entries + rows).
-std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::vector<int32_t> &rowptr,
-                                 int ctas) {
-    const int nt = (int)tiles.size() - 1;
-    std::vector<double> prefix(nt + 1, 0.0);
-    for (int t = 0; t < nt; ++t) {
-        const double nnz = rowptr[tiles[t + 1]] - rowptr[tiles[t]];
-        const double rows = tiles[t + 1] - tiles[t];
-        prefix[t + 1] = prefix[t] + nnz + 2.0 * rows;
-    }
-    std::vector<int32_t> cut(ctas + 1, 0);
-    int t = 0;
-    for (int b = 1; b < ctas; ++b) {
-        const double target = prefix[nt] * b / ctas;
-        while (t < nt && prefix[t + 1] <= target) ++t;
-        // choose the boundary closer to the target
-        if (t < nt && target - prefix[t] > prefix[t + 1] - target) ++t;
-        cut[b] = std::max(cut[b - 1], t);
-    }
-    cut[ctas] = nt;
-    return cut;
-}
-
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -356,6 +497,8 @@ Params base_params(const cg_handle *h) {
     P.colidx = h->colidx;
     P.vals = h->vals;
     P.tiles = h->tiles;
+    P.lcol = h->lcol;
+    P.segs = h->segs;
     P.cta_tile = h->cta_tile;
     P.cta_row = h->cta_row;
     P.dinv = h->dinv;
@@ -387,7 +530,7 @@ int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess) {
         void *args[] = {&P};
-        e = cudaLaunchCooperativeKernel((const void *)cg_solve_kernel, dim3(h->ctas), dim3(kThreads),
+        e = cudaLaunchCooperativeKernel((const void *)h->kernel, dim3(h->ctas), dim3(kThreads),
                                         args, (size_t)kSmemBytes, h->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
@@ -442,6 +585,7 @@ int cg_opts_default(cg_opts *opts) {
     opts->wait_limit_s = 5.0;
     opts->grid_ctas = 0;
     opts->debug_phantom_arrivals = 0;
+    opts->vectors_in_memory = 0;
     return CG_OK;
 }
 
@@ -474,6 +618,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         return CG_EINVAL;
     if (opts.grid_ctas < 0 || opts.debug_phantom_arrivals < 0 || opts.debug_phantom_arrivals > 1024)
         return CG_EINVAL;
+    if (opts.vectors_in_memory != 0 && opts.vectors_in_memory != 1) return CG_EINVAL;
     const int32_t n = A->n;
     const int64_t nnz = A->nnz;
     if (n < 0 || nnz < 0 || nnz > (int64_t)INT32_MAX - 64) return CG_EINVAL;
@@ -544,12 +689,15 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     h->max_tile_nnz = max_tile;
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return fail(CG_ECUDA);
-    if (cudaFuncSetAttribute((const void *)cg_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute((const void *)spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    for (int rpt : kRptChoices) {
+        if (cudaFuncSetAttribute((const void *)solve_kernel_for(rpt),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
+            return fail(CG_ECUDA);
+    }
+    if (cudaFuncSetAttribute((const void *)spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmemBytes) != cudaSuccess)
         return fail(CG_ECUDA);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_solve_kernel, kThreads, kSmemBytes) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(4), kThreads, kSmemBytes) !=
             cudaSuccess ||
         per_sm < 1)
         return fail(CG_ECUDA);
@@ -558,9 +706,21 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     ctas = std::max(1, std::min(ctas, std::max(1, h->ntiles)));
     h->ctas = ctas;
     std::vector<int32_t> cut = split_tiles(tiles, rowptr, ctas);
-    std::vector<int4> desc(std::max(1, h->ntiles));
-    for (int t = 0; t < h->ntiles; ++t)
-        desc[t] = make_int4(tiles[t], tiles[t + 1], rowptr[tiles[t]], rowptr[tiles[t + 1]]);
+    // rows per thread: warp 0 of the CTA with the most tiles owns the most
+    int max_tiles = 0;
+    for (int c = 0; c < ctas; ++c) max_tiles = std::max(max_tiles, cut[c + 1] - cut[c]);
+    const int per_warp = (max_tiles + kWarps - 1) / kWarps;
+    h->rpt = 0;
+    if (!opts.vectors_in_memory) {
+        for (int rpt : kRptChoices)
+            if (rpt > 0 && per_warp <= rpt) {
+                h->rpt = rpt;
+                break;
+            }
+    }
+    h->kernel = solve_kernel_for(h->rpt);
+    TilePlan tp = plan_windows(n, rowptr, colidx, tiles);
+    h->window_tiles = tp.windowed;
     std::vector<int32_t> cta_row(ctas + 1);
     for (int c = 0; c <= ctas; ++c) cta_row[c] = tiles[cut[c]];
 
@@ -575,14 +735,16 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     if ((rc = dev_alloc(h, &h->rowptr, (size_t)n + 1 + pad)) ||
         (rc = dev_alloc(h, &h->colidx, (size_t)nnz + pad)) ||
         (rc = dev_alloc(h, &h->vals, (size_t)nnz + pad)) ||
-        (rc = dev_alloc(h, &h->tiles, desc.size())) ||
+        (rc = dev_alloc(h, &h->tiles, tp.desc.size())) ||
+        (rc = dev_alloc(h, &h->segs, tp.segs.size())) ||
+        (rc = dev_alloc(h, &h->lcol, tp.lcol.size())) ||
         (rc = dev_alloc(h, &h->cta_tile, cut.size())) ||
         (rc = dev_alloc(h, &h->cta_row, cta_row.size())) ||
         (rc = dev_alloc(h, &h->r, (size_t)n)) ||
-        (rc = dev_alloc(h, &h->p0, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->p0, (size_t)n + pad)) ||
         (rc = dev_alloc(h, &h->q, (size_t)n)) ||
         (rc = dev_alloc(h, &h->b_dev, (size_t)n)) ||
-        (rc = dev_alloc(h, &h->x_dev, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->x_dev, (size_t)n + pad)) ||
         (rc = dev_alloc(h, &h->partials, (size_t)2 * ctas * kRedSlots)) ||
         (rc = dev_alloc(h, &h->bar, 64)) ||
         (rc = dev_alloc(h, &h->st, 1)))
@@ -606,7 +768,13 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     if (e == cudaSuccess && nnz > 0)
         e = cudaMemcpy(h->vals, vals.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(h->tiles, desc.data(), sizeof(int4) * desc.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(h->tiles, tp.desc.data(), sizeof(I4) * tp.desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->segs, tp.segs.data(), sizeof(I4) * tp.segs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->lcol, tp.lcol.data(), sizeof(uint16_t) * tp.lcol.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->p0, 0, sizeof(double) * (n + pad));
+    if (e == cudaSuccess) e = cudaMemset(h->x_dev, 0, sizeof(double) * (n + pad));
     if (e == cudaSuccess)
         e = cudaMemcpy(h->cta_tile, cut.data(), sizeof(int32_t) * cut.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -627,7 +795,15 @@ int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit
     }
     DeviceGuard g(h->device);
     if (maxit <= 0) maxit = h->n;
-    if ((rc = enqueue_solve(h, b, x, tol, maxit)) != CG_OK) return rc;
+    // The solve works on the handle's padded, 16-byte aligned copy of x (the
+    // TMA copies of x-windows need that alignment), copied in and out on the
+    // stream.
+    const size_t bytes = sizeof(double) * (size_t)h->n;
+    if (cudaMemcpyAsync(h->x_dev, x, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return CG_ECUDA;
+    if ((rc = enqueue_solve(h, b, h->x_dev, tol, maxit)) != CG_OK) return rc;
+    if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return CG_ECUDA;
     return finish_solve(h, info);
 }
 
@@ -657,6 +833,13 @@ int cg_spmv(cg_handle *h, const double *x, double *y) {
     DeviceGuard g(h->device);
     Params P = base_params(h);
     P.x = const_cast<double *>(x);
+    if (reinterpret_cast<uintptr_t>(x) % 16 != 0) {
+        // x-windows are TMA copies and need a 16-byte aligned source
+        if (cudaMemcpyAsync(h->x_dev, x, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToDevice,
+                            h->stream) != cudaSuccess)
+            return CG_ECUDA;
+        P.x = h->x_dev;
+    }
     P.q = y;
     spmv_kernel<<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
@@ -675,6 +858,8 @@ int cg_get_plan(const cg_handle *h, cg_plan *plan) {
     p.smem_bytes = kSmemBytes;
     p.lanes_per_row = 1;
     p.l2_evict_first = h->evict_first;
+    p.reg_rows = h->rpt;
+    p.window_tiles = h->window_tiles;
     p.device_bytes = h->device_bytes;
     *plan = p;
     return CG_OK;

@@ -1,0 +1,229 @@
+// Host-side planning of the SpMV tiles (plain C++, no CUDA calls): row
+// tiles, their x-windows and 16-bit local columns, the split of tiles over
+// CTAs, and a checker of every index the kernels derive from the plan.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "layout.h"
+
+namespace gbcg {
+
+struct I4 {
+    int32_t x, y, z, w;
+};
+inline I4 mk4(int32_t x, int32_t y, int32_t z, int32_t w) { return I4{x, y, z, w}; }
+
+// Row tiles: at most kTileRows rows and kTileNnz entries each; a row with
+// more than kTileNnz entries is a tile of its own (read from global memory).
+std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, int *max_nnz) {
+    std::vector<int32_t> tiles;
+    tiles.reserve(n / 16 + 2);
+    int32_t r = 0;
+    *max_nnz = 0;
+    while (r < n) {
+        const int32_t start = r;
+        if (rowptr[r + 1] - rowptr[r] > kTileNnz) {
+            ++r;
+        } else {
+            while (r < n && r - start < kTileRows && rowptr[r + 1] - rowptr[r] <= kTileNnz &&
+                   rowptr[r + 1] - rowptr[start] <= kTileNnz)
+                ++r;
+        }
+        tiles.push_back(start);
+        *max_nnz = std::max(*max_nnz, rowptr[r] - rowptr[start]);
+    }
+    tiles.push_back(n);
+    return tiles;
+}
+
+// x-window of one tile: the distinct columns grouped into runs (gaps of up
+// to kGap unused columns are bridged), each run widened to 16-byte (2
+// double) boundaries; a run that would end past the vector's last column
+// (n odd) stops short and names that column as its tail.  Windowed when the
+// runs fit kSegMax lanes and kWinMax doubles; each entry then stores its
+// 16-bit offset in the window.
+constexpr int kGap = 4;
+
+struct TilePlan {
+    std::vector<I4> desc;       // 2 per tile
+    std::vector<I4> segs;
+    std::vector<uint16_t> lcol;   // nnz (+ padding)
+    int windowed = 0;
+};
+
+TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
+                      const std::vector<int32_t> &tiles) {
+    TilePlan tp;
+    const int nt = (int)tiles.size() - 1;
+    tp.desc.resize(2 * (size_t)std::max(nt, 1), mk4(0, 0, 0, 0));
+    tp.lcol.assign(colidx.size() + 32, 0);
+    std::vector<int32_t> cols;
+    std::vector<I4> runs;
+    for (int t = 0; t < nt; ++t) {
+        const int r0 = tiles[t], r1 = tiles[t + 1];
+        const int a = rowptr[r0], e = rowptr[r1];
+        int kind = kTileGather, seg0 = 0, nseg = 0, wtx = 0;
+        if (e - a > kTileNnz) {
+            kind = kTileLong;
+        } else if (e > a) {
+            cols.assign(colidx.begin() + a, colidx.begin() + e);
+            std::sort(cols.begin(), cols.end());
+            cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+            // runs [first, last] of columns, bridged over small gaps, aligned
+            runs.clear();
+            int first = cols[0], last = cols[0];
+            auto flush = [&]() {
+                const int gs = first & ~1;
+                int ge = (last + 2) & ~1;  // exclusive, even
+                if (!runs.empty() && gs <= runs.back().y) {
+                    runs.back().y = std::max(runs.back().y, ge);
+                } else {
+                    runs.push_back(mk4(gs, ge, 0, 0));
+                }
+            };
+            for (size_t i = 1; i < cols.size(); ++i) {
+                if (cols[i] - last <= kGap + 1) {
+                    last = cols[i];
+                } else {
+                    flush();
+                    first = last = cols[i];
+                }
+            }
+            flush();
+            // window layout
+            int woff = 0, tx = 0;
+            std::vector<I4> segs;
+            for (const I4 &rr : runs) {
+                I4 sg;
+                sg.x = rr.x;
+                sg.y = woff;
+                if (rr.y > n) {  // runs to n + 1: n odd, stop before the last column
+                    sg.z = (n - 1) - rr.x;
+                    sg.w = n - 1;
+                } else {
+                    sg.z = rr.y - rr.x;
+                    sg.w = -1;
+                }
+                woff += rr.y - rr.x;
+                tx += sg.z;
+                segs.push_back(sg);
+            }
+            if ((int)segs.size() <= kSegMax && woff <= kWinMax) {
+                kind = kTileWindow;
+                seg0 = (int)tp.segs.size();
+                nseg = (int)segs.size();
+                wtx = tx;
+                tp.segs.insert(tp.segs.end(), segs.begin(), segs.end());
+                for (int k = a; k < e; ++k) {
+                    const int c = colidx[k];
+                    // the run holding c (runs are sorted and disjoint)
+                    int lo = 0, hi = nseg - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) / 2;
+                        if (segs[mid].x <= c) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    tp.lcol[k] = (uint16_t)(segs[lo].y + (c - segs[lo].x));
+                }
+                ++tp.windowed;
+            }
+        }
+        tp.desc[2 * t] = mk4(r0, r1, a, e);
+        tp.desc[2 * t + 1] = mk4(seg0, nseg, wtx, kind);
+    }
+    if (tp.segs.empty()) tp.segs.push_back(mk4(0, 0, 0, -1));
+    return tp;
+}
+
+// Contiguous tile ranges per CTA with about equal cost (entries + rows).
+std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::vector<int32_t> &rowptr,
+                                 int ctas) {
+    const int nt = (int)tiles.size() - 1;
+    std::vector<double> prefix(nt + 1, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        const double nnz = rowptr[tiles[t + 1]] - rowptr[tiles[t]];
+        const double rows = tiles[t + 1] - tiles[t];
+        prefix[t + 1] = prefix[t] + nnz + 2.0 * rows;
+    }
+    std::vector<int32_t> cut(ctas + 1, 0);
+    int t = 0;
+    for (int b = 1; b < ctas; ++b) {
+        const double target = prefix[nt] * b / ctas;
+        while (t < nt && prefix[t + 1] <= target) ++t;
+        // choose the boundary closer to the target
+        if (t < nt && target - prefix[t] > prefix[t + 1] - target) ++t;
+        cut[b] = std::max(cut[b - 1], t);
+    }
+    cut[ctas] = nt;
+    return cut;
+}
+
+
+// Checks every address the kernels form from a plan: TMA source ranges inside
+// the (padded) arrays, copy sizes inside the stage regions, window segments
+// aligned and inside [0, n), and each windowed entry's local column pointing
+// back at its global column.  Returns an empty string when the plan is sound.
+inline std::string check_plan(int32_t n, const std::vector<int32_t> &rowptr,
+                              const std::vector<int32_t> &colidx, const std::vector<int32_t> &tiles,
+                              const TilePlan &tp, int64_t pad) {
+    const int64_t nnz = (int64_t)colidx.size();
+    const int nt = (int)tiles.size() - 1;
+    auto err = [](int t, const char *what) { return "tile " + std::to_string(t) + ": " + what; };
+    for (int t = 0; t < nt; ++t) {
+        const I4 d0 = tp.desc[2 * t], d1 = tp.desc[2 * t + 1];
+        const int r0 = d0.x, r1 = d0.y, a = d0.z, e = d0.w, seg0 = d1.x, nseg = d1.y, wtx = d1.z, kind = d1.w;
+        if (r0 != tiles[t] || r1 != tiles[t + 1] || a != rowptr[r0] || e != rowptr[r1]) return err(t, "descriptor");
+        if (r1 <= r0 || r1 - r0 > kTileRows) return err(t, "rows");
+        if (kind == kTileLong) {
+            if (r1 - r0 != 1 || e - a <= kTileNnz) return err(t, "long row");
+            continue;
+        }
+        if (e - a > kTileNnz) return err(t, "entries");
+        const int ra = r0 & ~3, re = (r1 + 1 + 3) & ~3;
+        if (ra < 0 || re > n + 1 + pad || re - ra > kRptrStage) return err(t, "row pointer copy");
+        if (e > a) {
+            const int va = a & ~1, ve = (e + 1) & ~1;
+            if (va < 0 || ve > nnz + pad || ve - va > kValsStage) return err(t, "value copy");
+            if (kind == kTileWindow) {
+                const int ca = a & ~7, ce = (e + 7) & ~7;
+                if (ca < 0 || ce > nnz + 32 || (ce - ca) * 2 > kColsStage * 4) return err(t, "local column copy");
+            } else {
+                const int ca = a & ~3, ce = (e + 3) & ~3;
+                if (ca < 0 || ce > nnz + pad || ce - ca > kColsStage) return err(t, "column copy");
+            }
+        }
+        if (kind != kTileWindow) {
+            if (nseg != 0 || wtx != 0) return err(t, "window on a gather tile");
+            continue;
+        }
+        if (nseg < 1 || nseg > kSegMax || seg0 < 0 || seg0 + nseg > (int)tp.segs.size()) return err(t, "segments");
+        int tx = 0, slots_end = 0;
+        for (int i = 0; i < nseg; ++i) {
+            const I4 sg = tp.segs[seg0 + i];
+            if (sg.x < 0 || (sg.x & 1) || (sg.y & 1) || sg.z < 0 || (sg.z & 1)) return err(t, "segment alignment");
+            if (sg.y != slots_end) return err(t, "segment offsets");
+            if (sg.x + sg.z > n) return err(t, "segment past the vector");
+            if (sg.w >= 0 && (sg.w != sg.x + sg.z || sg.w != n - 1)) return err(t, "tail column");
+            if (i > 0 && sg.x < tp.segs[seg0 + i - 1].x + tp.segs[seg0 + i - 1].z) return err(t, "segment order");
+            slots_end = sg.y + sg.z + (sg.w >= 0 ? 2 : 0);
+            tx += sg.z;
+        }
+        if (tx != wtx || slots_end > kWinMax) return err(t, "window size");
+        for (int k = a; k < e; ++k) {
+            const int lc = tp.lcol[k];
+            if (lc >= slots_end) return err(t, "local column outside the window");
+            int i = nseg - 1;
+            while (i > 0 && tp.segs[seg0 + i].y > lc) --i;
+            const I4 sg = tp.segs[seg0 + i];
+            const int col = lc - sg.y < sg.z ? sg.x + (lc - sg.y) : (lc - sg.y == sg.z ? sg.w : -2);
+            if (col != colidx[k]) return err(t, "local column maps to the wrong column");
+        }
+    }
+    return std::string();
+}
+
+}  // namespace gbcg

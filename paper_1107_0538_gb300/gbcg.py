@@ -44,7 +44,7 @@ class cg_csr(ctypes.Structure):
 class cg_opts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("true_residual", ctypes.c_int32),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int32),
-                ("debug_phantom_arrivals", ctypes.c_int32)]
+                ("debug_phantom_arrivals", ctypes.c_int32), ("vectors_in_memory", ctypes.c_int32)]
 
 
 class cg_info(ctypes.Structure):
@@ -61,6 +61,7 @@ class cg_plan(ctypes.Structure):
                 ("threads", ctypes.c_int32), ("tiles", ctypes.c_int32), ("tile_nnz", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("l2_evict_first", ctypes.c_int32),
+                ("reg_rows", ctypes.c_int32), ("window_tiles", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
@@ -181,7 +182,7 @@ class Solver:
 
     def __init__(self, A, precond: int = CG_PRECOND_NONE, true_residual: bool = True,
                  wait_limit_s: float = 5.0, grid_ctas: int = 0, debug_phantom_arrivals: int = 0,
-                 stream=None):
+                 vectors_in_memory: bool = False, stream=None):
         import torch
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -191,6 +192,7 @@ class Solver:
         o.wait_limit_s = wait_limit_s
         o.grid_ctas = grid_ctas
         o.debug_phantom_arrivals = debug_phantom_arrivals
+        o.vectors_in_memory = 1 if vectors_in_memory else 0
         csr, self._keep = host_csr(A)
         rc, self.h = cg_create(csr, o, self.stream.cuda_stream)
         if rc != CG_OK:

@@ -54,12 +54,12 @@ int main(void) {
   printf("{");
   F(cg_csr, n) F(cg_csr, nnz) F(cg_csr, rowptr) F(cg_csr, colidx) F(cg_csr, vals) F(cg_csr, mem)
   F(cg_opts, precond) F(cg_opts, true_residual) F(cg_opts, wait_limit_s) F(cg_opts, grid_ctas)
-  F(cg_opts, debug_phantom_arrivals)
+  F(cg_opts, debug_phantom_arrivals) F(cg_opts, vectors_in_memory)
   F(cg_info, iters) F(cg_info, status) F(cg_info, relres) F(cg_info, relres_true)
   F(cg_info, kernel_ms) F(cg_info, launches) F(cg_info, reserved)
   F(cg_plan, n) F(cg_plan, nnz) F(cg_plan, ctas) F(cg_plan, threads) F(cg_plan, tiles)
   F(cg_plan, tile_nnz) F(cg_plan, stages) F(cg_plan, smem_bytes) F(cg_plan, lanes_per_row)
-  F(cg_plan, l2_evict_first) F(cg_plan, device_bytes)
+  F(cg_plan, l2_evict_first) F(cg_plan, reg_rows) F(cg_plan, window_tiles) F(cg_plan, device_bytes)
   printf("\\"sizes\\": [%zu, %zu, %zu, %zu]}", sizeof(cg_csr), sizeof(cg_opts), sizeof(cg_info), sizeof(cg_plan));
   return 0;
 }
@@ -124,7 +124,8 @@ def test_bad_options_rejected_without_gpu():
     A = problems.cube_uniform(2).A
     c, keep = gbcg.host_csr(A)
     for field, value in [("precond", 3), ("wait_limit_s", 0.0), ("wait_limit_s", float("nan")),
-                         ("grid_ctas", -1), ("debug_phantom_arrivals", -2)]:
+                         ("grid_ctas", -1), ("debug_phantom_arrivals", -2),
+                         ("vectors_in_memory", 2)]:
         o = gbcg.cg_opts_default()
         setattr(o, field, value)
         rc, h = gbcg.cg_create(c, o, None)

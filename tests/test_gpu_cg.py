@@ -133,10 +133,11 @@ def test_spmv_parity(dev, case):
 
 # -------------------------------------------------------------- CG parity
 
-def test_cg_uniform_cube_full_solve(dev):
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
+def test_cg_uniform_cube_full_solve(dev, mem):
     pr = problem("c1")
     ref = oracle_full("c1")
-    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol)
+    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, vectors_in_memory=mem)
     assert ref["status"] == oracle.OK and info.status == gbcg.CG_OK
     assert abs(info.iters - ref["iters"]) <= 2
     assert rel(x, ref["x"]) <= 1e-10
@@ -144,22 +145,24 @@ def test_cg_uniform_cube_full_solve(dev):
     assert info.relres_true <= 1.01 * pr.tol
 
 
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
 @pytest.mark.parametrize("precond,k", [(0, 200), (0, 350), (1, 150)])
-def test_cg_paper_sized_fixed_k_iterates(dev, precond, k):
+def test_cg_paper_sized_fixed_k_iterates(dev, precond, k, mem):
     pr = problem("c2")
     ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=k, precond=precond)
-    x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=k, precond=precond)
+    x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=k, precond=precond, vectors_in_memory=mem)
     assert info.status == gbcg.CG_ENOCONV and ref["status"] == oracle.ENOCONV
     assert info.iters == k == ref["iters"]
     assert rel(x, ref["x"]) <= 1e-10
     assert abs(info.relres - ref["relres"]) <= 1e-6 * ref["relres"]
 
 
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
 @pytest.mark.parametrize("precond", [0, 1])
-def test_cg_paper_sized_full_solve(dev, precond):
+def test_cg_paper_sized_full_solve(dev, precond, mem):
     pr = problem("c2")
     ref = oracle_full("c2", precond)
-    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, precond=precond)
+    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, precond=precond, vectors_in_memory=mem)
     assert ref["status"] == oracle.OK and info.status == gbcg.CG_OK
     assert abs(info.iters - ref["iters"]) <= max(2, 0.02 * ref["iters"])
     assert info.relres <= pr.tol and info.relres_true <= 1.05 * pr.tol
@@ -182,9 +185,10 @@ def test_cg_large_fixed_k_and_full_solve(dev):
 
 # ------------------------------------------------------------- edge cases
 
-def test_zero_rhs(dev):
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
+def test_zero_rhs(dev, mem):
     pr = problem("small")
-    x, info = gpu_solve(pr.A, np.zeros(pr.A.n), dev, 1e-8, x0=np.ones(pr.A.n))
+    x, info = gpu_solve(pr.A, np.zeros(pr.A.n), dev, 1e-8, x0=np.ones(pr.A.n), vectors_in_memory=mem)
     assert info.status == gbcg.CG_OK and info.iters == 0 and np.all(x == 0)
 
 
@@ -196,10 +200,11 @@ def test_nan_rhs(dev):
     assert info.status == gbcg.CG_ENAN
 
 
-def test_maxit_returns_last_iterate(dev):
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
+def test_maxit_returns_last_iterate(dev, mem):
     pr = problem("small")
     ref = oracle.cg(pr.A, pr.b, tol=1e-14, maxit=7)
-    x, info = gpu_solve(pr.A, pr.b, dev, 1e-14, maxit=7)
+    x, info = gpu_solve(pr.A, pr.b, dev, 1e-14, maxit=7, vectors_in_memory=mem)
     assert info.status == gbcg.CG_ENOCONV == ref["status"] and info.iters == 7
     assert rel(x, ref["x"]) <= 1e-12
 
@@ -218,14 +223,15 @@ def test_single_unknown(dev):
     assert info.status == gbcg.CG_OK and info.iters == 1 and x[0] == 0.5
 
 
-def test_nonzero_initial_guess_and_already_converged(dev):
+@pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
+def test_nonzero_initial_guess_and_already_converged(dev, mem):
     pr = problem("small")
     ref = oracle.cg(pr.A, pr.b, tol=1e-12)
     x0 = ref["x"] + 1e-3
     r2 = oracle.cg(pr.A, pr.b, x0=x0, tol=1e-12)
-    x, info = gpu_solve(pr.A, pr.b, dev, 1e-12, x0=x0)
+    x, info = gpu_solve(pr.A, pr.b, dev, 1e-12, x0=x0, vectors_in_memory=mem)
     assert abs(info.iters - r2["iters"]) <= 2 and rel(x, r2["x"]) <= 1e-10
-    x, info = gpu_solve(pr.A, pr.b, dev, 1e-2, x0=ref["x"])
+    x, info = gpu_solve(pr.A, pr.b, dev, 1e-2, x0=ref["x"], vectors_in_memory=mem)
     assert info.status == gbcg.CG_OK and info.iters == 0
 
 
@@ -287,13 +293,19 @@ def test_device_resident_csr_input(dev):
         gbcg.cg_destroy(h)
 
 
-def test_plan(dev):
+def test_plan_and_vector_modes(dev):
+    with gbcg.Solver(problem("c3").A) as s:
+        assert s.plan()["reg_rows"] == 0          # too many rows per thread
+    with gbcg.Solver(problem("c2").A, vectors_in_memory=True) as s:
+        assert s.plan()["reg_rows"] == 0
     pr = problem("c2")
     with gbcg.Solver(pr.A) as s:
         p = s.plan()
+    assert p["reg_rows"] in (1, 2, 4)
+    assert p["window_tiles"] == p["tiles"]  # every stencil tile stages its x-window
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert 1 <= p["ctas"] <= sms and p["tiles"] >= p["ctas"]
-    assert p["tile_nnz"] <= 1024 and p["n"] == pr.A.n and p["nnz"] == pr.A.nnz
+    assert p["tile_nnz"] <= 896 and p["n"] == pr.A.n and p["nnz"] == pr.A.nnz
 
 
 def test_solve_argument_errors(dev):
