@@ -305,17 +305,28 @@ def run_gbcg(args) -> None:
     solver.close()
 
     if not args.no_extras:
-        # --------------------------------------------- Jacobi-PCG form
-        ps = gbcg.Solver(pr.A, precond=gbcg.CG_PRECOND_JACOBI)
-        timed_solves(ps, b, x, 2, False)
-        pres = timed_solves(ps, b, x, max(3, args.steps // 2), True)
-        p_ms = statistics.mean(t for t, _ in pres)
-        ps.close()
-        line["forms"] = {
-            "fp64_cg": {"ms_per_solve": round(ms_per_step, 4), "iters": iters},
-            "jacobi_pcg": {"ms_per_solve": round(p_ms, 4), "iters": pres[-1][1].iters,
-                           "speedup_vs_fp64_cg": round(ms_per_step / p_ms, 3)},
-        }
+        # ------------------------------- Jacobi-PCG and mixed-precision forms
+        import oracle
+        ref_x = oracle.cg(pr.A, pr.b, tol=TOL)["x"]
+        forms = {"fp64_cg": {"ms_per_solve": round(ms_per_step, 4), "iters": iters}}
+        variants = [("jacobi_pcg", dict(precond=gbcg.CG_PRECOND_JACOBI)),
+                    ("fp32_ir", dict(inner_values=gbcg.CG_VALUES_FP32)),
+                    ("bf16_ir", dict(inner_values=gbcg.CG_VALUES_BF16)),
+                    ("fp32_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI)),
+                    ("bf16_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_BF16, precond=gbcg.CG_PRECOND_JACOBI))]
+        for name, kw in variants:
+            vs = gbcg.Solver(pr.A, **kw)
+            timed_solves(vs, b, x, 2, False)
+            res_v = timed_solves(vs, b, x, max(3, args.steps // 2), True)
+            v_ms = statistics.mean(t for t, _ in res_v)
+            xv = x.cpu().numpy()
+            info_v = res_v[-1][1]
+            forms[name] = {"ms_per_solve": round(v_ms, 4), "iters": info_v.iters, "outer": info_v.outer,
+                           "relres_true": info_v.relres_true,
+                           "err_vs_fp64_oracle": float(np.linalg.norm(xv - ref_x) / np.linalg.norm(ref_x)),
+                           "speedup_vs_fp64_cg": round(ms_per_step / v_ms, 3)}
+            vs.close()
+        line["forms"] = forms
         # -------------------------------------- SpMV roofline at 100^3 (HBM)
         big = problems.cube_blobs(100)
         bs = gbcg.Solver(big.A)

@@ -53,6 +53,11 @@ extern "C" {
 #define CG_MEM_HOST 0
 #define CG_MEM_DEVICE 1
 
+/* ---- precision of the inner solve --------------------------------------- */
+#define CG_VALUES_FP64 0     /* plain FP64 CG (the paper's double precision)      */
+#define CG_VALUES_FP32 1     /* FP32 inner CG on FP32 values + FP64 refinement    */
+#define CG_VALUES_BF16 2     /* FP32 inner CG on BF16 values + FP64 refinement    */
+
 /* ---- preconditioners --------------------------------------------------- */
 #define CG_PRECOND_NONE 0    /* plain CG, as in Section IV                      */
 #define CG_PRECOND_JACOBI 1  /* z = diag(A)^-1 r (Jacobi-preconditioned CG)     */
@@ -91,17 +96,32 @@ typedef struct {
                                 rows, the solver keeps x, r, z, p, q and 1/diag of
                                 those rows in registers for the whole solve;
                                 1: always keep every vector in device memory     */
+    int32_t inner_values;    /* CG_VALUES_*; default CG_VALUES_FP64.  FP32/BF16
+                                turn the solve into iterative refinement: the
+                                outer loop keeps x and r = b - A x in FP64 with
+                                the FP64 matrix and stops on the true residual;
+                                each correction solves A_lo d = r by CG in FP32
+                                on a copy of A whose off-diagonals are rounded
+                                (nearest-even) to FP32/BF16 and whose FP32
+                                diagonal is row-sum compensated (A_lo keeps A's
+                                row sums); precond applies to the inner CG     */
+    double inner_tol;        /* inner stop: ||r_in|| <= inner_tol ||r||; 0 =
+                                1e-3 (FP32) or 1e-2 (BF16)                      */
+    int32_t max_outer;       /* refinement steps at most; default 50             */
+    int32_t max_inner;       /* inner iterations per step at most; 0 = n         */
 } cg_opts;
 
 /* Result of a solve (also returned through the status code). */
 typedef struct {
-    int32_t iters;           /* products A p inside the loop (x updates applied) */
+    int32_t iters;           /* products A p inside the loop (x updates applied);
+                                with refinement: inner iterations, all steps    */
     int32_t status;          /* same value as the function's return code         */
-    double relres;           /* ||r_k||_2 / ||b||_2 of the recursive residual     */
+    double relres;           /* ||r_k||_2 / ||b||_2 of the recursive residual
+                                (with refinement: of the FP64 outer residual)   */
     double relres_true;      /* ||b - A x||_2 / ||b||_2 if requested, else -1     */
     double kernel_ms;        /* device time of the solve kernel (CUDA events)     */
     int32_t launches;        /* kernels this call launched                        */
-    int32_t reserved;
+    int32_t outer;           /* refinement steps applied (0 for plain CG)         */
 } cg_info;
 
 /* Read-only description of the launch plan of a handle. */
@@ -147,7 +167,8 @@ int cg_create(const cg_csr *A, const cg_opts *opts, void *stream, cg_handle **ou
  * Runs CG from x (in: x0, out: the last iterate) until
  * ||r_k||_2 <= tol * ||b||_2 (the continue-condition of Section IV; Table I
  * uses tol = 1e-10) or maxit iterations (maxit <= 0 means n: "a 132651 loop",
- * Section IV).  b and x are device pointers of length n; b must not alias x.
+ * Section IV).  With inner_values FP32/BF16 the stop test is on the true
+ * FP64 residual and maxit caps the inner iterations of all steps together.  b and x are device pointers of length n; b must not alias x.
  * b = 0 gives x = 0 after 0 iterations.  Synchronous: returns after the
  * result is on the device and the status is read back.  info may be NULL.
  * Returns CG_OK, CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT, CG_EINVAL

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "gbcg.h"
@@ -20,7 +21,7 @@ struct DevStatus {
     double bb;        // ||b||^2
     double true_rr;   // ||b - A x||^2 (if computed)
     int32_t where;    // diagnostic: which wait timed out (0 = none)
-    int32_t pad;
+    int32_t outer;    // refinement steps (mixed precision)
 };
 
 // Everything a kernel needs, passed by value.
@@ -29,6 +30,18 @@ struct Params {
     const int32_t *__restrict__ rowptr;
     const int32_t *__restrict__ colidx;   // padded to a multiple of 4 + slack
     const double *__restrict__ vals;      // padded to a multiple of 2 + slack
+    const float *__restrict__ vals32;     // inner values, FP32 (mixed precision)
+    const __nv_bfloat16 *__restrict__ vals16;  // inner values, BF16 (mixed precision)
+    const float *__restrict__ diag_lo;    // inner diagonal (FP32, row-sum compensated)
+    const float *__restrict__ dinv32;     // 1 / diag_lo (inner Jacobi)
+    float *r32;         // inner residual
+    float *z32;         // inner preconditioned residual (== r32 without Jacobi)
+    float *p32;         // inner direction (padded, 16-byte aligned: window source)
+    float *q32;         // A_lo p
+    float *d32;         // inner correction
+    double inner_tol;
+    int32_t max_outer;
+    int32_t max_inner;
     const int4 *__restrict__ tiles;       // 2 x ntiles int4 (TileDesc)
     const uint16_t *__restrict__ lcol;    // local column of each entry (windowed tiles)
     const int4 *__restrict__ segs;        // window segments: {first column (even), window offset,
@@ -308,15 +321,25 @@ struct Pipe {
     uint32_t win_issued = 0;  // tiles whose window part is issued
 };
 
-// Matrix part of tile t into stage s (lane 0).
-__device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, const TileDesc &d, int s) {
+// Conversions of stored values to the accumulation type.
+__device__ __forceinline__ double to_acc(double v, double) { return v; }
+__device__ __forceinline__ float to_acc(float v, float) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+
+// Matrix part of a tile into stage s (lane 0): values (type VT), column
+// indices, row pointers; the mbarrier also expects the tile's window of XT
+// elements.
+template <class VT, class XT>
+__device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, const TileDesc &d, int s,
+                                             const VT *vals) {
     if (d.kind == kTileLong) {
         mbar_arrive(&S.mbar[s]);
         return;
     }
-    const int va = d.a & ~1, ve = (d.e + 1) & ~1;   // 16-byte aligned ranges
+    constexpr int epb = 16 / (int)sizeof(VT);        // values per 16 bytes
+    const int va = d.a & ~(epb - 1), ve = (d.e + epb - 1) & ~(epb - 1);
     const int ra = d.r0 & ~3, re = (d.r1 + 1 + 3) & ~3;
-    const uint32_t vbytes = (uint32_t)(ve - va) * 8u, rbytes = (uint32_t)(re - ra) * 4u;
+    const uint32_t vbytes = (uint32_t)(ve - va) * (uint32_t)sizeof(VT), rbytes = (uint32_t)(re - ra) * 4u;
     uint32_t cbytes;
     const void *csrc;
     if (d.kind == kTileWindow) {
@@ -328,12 +351,11 @@ __device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, con
         cbytes = (uint32_t)(ce - ca) * 4u;
         csrc = P.colidx + ca;
     }
-    // the window bytes the TMA will deliver (a tail column, if any, is stored
-    // by a thread instead)
-    const uint32_t wbytes = (uint32_t)d.wtx * 8u;
+    // window bytes the TMA will deliver (tail columns are stored by threads)
+    const uint32_t wbytes = (uint32_t)d.wtx * (uint32_t)sizeof(XT);
     mbar_arrive_expect_tx(&S.mbar[s], (d.e > d.a ? vbytes + cbytes : 0u) + rbytes + wbytes);
     if (d.e > d.a) {
-        tma_load_1d(S.vals(s), P.vals + va, vbytes, &S.mbar[s], P.evict_first != 0);
+        tma_load_1d(S.vals(s), vals + va, vbytes, &S.mbar[s], P.evict_first != 0);
         tma_load_1d(S.cols(s), csrc, cbytes, &S.mbar[s], P.evict_first != 0);
     }
     tma_load_1d(S.rptr(s), P.rowptr + ra, rbytes, &S.mbar[s], false);
@@ -341,27 +363,34 @@ __device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, con
 
 // Window part of a windowed tile into stage s: lane l copies segment l of
 // the vector x (16-byte aligned).
+template <class XT>
 __device__ __forceinline__ void issue_window(const Params &P, const Smem &S, const TileDesc &d, int s,
-                                             const double *x) {
+                                             const XT *x) {
     const int lane = threadIdx.x & 31;
     if (d.kind != kTileWindow || lane >= d.nseg) return;
     const int4 sg = __ldg(P.segs + d.seg0 + lane);
-    if (sg.z > 0) tma_load_1d(S.win(s) + sg.y, x + sg.x, (uint32_t)sg.z * 8u, &S.mbar[s], false);
+    if (sg.z > 0)
+        tma_load_1d(reinterpret_cast<XT *>(S.win(s)) + sg.y, x + sg.x, (uint32_t)sg.z * (uint32_t)sizeof(XT),
+                    &S.mbar[s], false);
 }
 
-// A segment ending on the vector's last column when n is odd would run one
-// element past the vector; its TMA copy stops short and its lane stores that
-// column into the window slot after the copied part.
+// A segment running past the vector's end stops at column n & ~3; its lane
+// stores the 1 to 3 columns after that into the window slots that follow.
+template <class XT>
 __device__ __forceinline__ void store_tail(const Params &P, const Smem &S, const TileDesc &d, int s,
-                                           const double *x) {
+                                           const XT *x) {
     const int lane = threadIdx.x & 31;
     if (d.kind != kTileWindow || lane >= d.nseg) return;
     const int4 sg = __ldg(P.segs + d.seg0 + lane);
-    if (sg.w >= 0) S.win(s)[sg.y + sg.z] = x[sg.w];
+    if (sg.w >= 0) {
+        XT *win = reinterpret_cast<XT *>(S.win(s));
+        for (int c = sg.w; c < P.n; ++c) win[sg.y + sg.z + (c - sg.w)] = x[c];
+    }
 }
 
+template <class VT, class XT>
 __device__ __forceinline__ void issue_next(const Params &P, const Smem &S, Pipe &pp, int t0, int m,
-                                           uint32_t limit, uint32_t pass_end, const double *x) {
+                                           uint32_t limit, uint32_t pass_end, const VT *vals, const XT *x) {
     const int w = threadIdx.x >> 5;
     if (pp.issued < pp.consumed + 1 && pp.issued < limit) {
         const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.issued % (uint32_t)m));
@@ -369,10 +398,10 @@ __device__ __forceinline__ void issue_next(const Params &P, const Smem &S, Pipe 
         // columns) before the async-proxy copies that will overwrite it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) issue_matrix(P, S, d, w);
+        if ((threadIdx.x & 31) == 0) issue_matrix<VT, XT>(P, S, d, w, vals);
         __syncwarp();
         if (pp.issued < pass_end) {  // same pass: the vector is final, load the window now
-            issue_window(P, S, d, w, x);
+            issue_window<XT>(P, S, d, w, x);
             ++pp.win_issued;
         }
         ++pp.issued;
@@ -381,16 +410,15 @@ __device__ __forceinline__ void issue_next(const Params &P, const Smem &S, Pipe 
 
 // Sum over one row: exactly one FMA per stored entry, the loads of a batch
 // issued before its first FMA, two interleaved accumulators.
-template <class Col, class Val>
-__device__ __forceinline__ double row_sum(int k0, int k1, const Col &col_of, const Val &val_of,
-                                          const double *vs) {
-    double s0 = 0.0, s1 = 0.0;
+template <class AT, class VT, class Col, class Val>
+__device__ __forceinline__ AT row_sum(int k0, int k1, const Col &col_of, const Val &val_of, const VT *vs) {
+    AT s0 = AT(0), s1 = AT(0);
     for (int kb = k0; kb < k1; kb += kBatch) {
-        double v[kBatch], xv[kBatch];
+        AT v[kBatch], xv[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int k = min(kb + u, k1 - 1);  // clamped: every load is in range
-            v[u] = vs[k];
+            v[u] = to_acc(vs[k], AT(0));
             xv[u] = val_of(col_of(k));
         }
 #pragma unroll
@@ -408,40 +436,42 @@ __device__ __forceinline__ double row_sum(int k0, int k1, const Col &col_of, con
 // epi.row(i, sum, j) for each row i of the tile (lane l gets row r0 + l; j is
 // the warp's local tile number in the pass).  Returns false if the wait ran
 // out.
-template <class Epi>
+template <class VT, class XT, class AT, class Epi>
 __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &pp, int t0, int m,
-                                          uint32_t limit, uint32_t pass_end, const double *x, Epi &epi,
-                                          int j) {
+                                          uint32_t limit, uint32_t pass_end, const VT *vals, const XT *x,
+                                          Epi &epi, int j) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t c = pp.consumed;
     const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(c % (uint32_t)m));
-    store_tail(P, S, d, w, x);  // nobody reads the stage before the wait below
+    store_tail<XT>(P, S, d, w, x);  // nobody reads the stage before the wait below
     const bool got = mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns);
     if (__any_sync(0xffffffffu, !got)) return false;
     __syncwarp();
     if (d.kind == kTileLong) {
         // one long row: the warp reduces it straight from global memory
-        double part = 0.0;
-        for (int k = d.a + lane; k < d.e; k += 32) part = fma(P.vals[k], x[P.colidx[k]], part);
-        part = warp_sum(part);
+        AT part = AT(0);
+        for (int k = d.a + lane; k < d.e; k += 32)
+            part = fma(to_acc(vals[k], AT(0)), AT(x[P.colidx[k]]), part);
+#pragma unroll
+        for (int mm = 16; mm >= 1; mm >>= 1) part += __shfl_xor_sync(0xffffffffu, part, mm);
         if (lane == 0) epi.row(d.r0, part, j);
     } else {
-        const double *vs = S.vals(w) - (d.a & ~1);
+        const VT *vs = reinterpret_cast<const VT *>(S.vals(w)) - (d.a & ~(16 / (int)sizeof(VT) - 1));
         const int32_t *rs = S.rptr(w) - (d.r0 & ~3);
         const int row = d.r0 + lane;
         if (row < d.r1) {
             const int k0 = rs[row], k1 = rs[row + 1];
-            double sum = 0.0;
+            AT sum = AT(0);
             if (k1 > k0) {
                 if (d.kind == kTileWindow) {
                     const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols(w)) - (d.a & ~7);
-                    const double *win = S.win(w);
-                    sum = row_sum(k0, k1, [&](int k) { return (int)lc[k]; },
-                                  [&](int c2) { return win[c2]; }, vs);
+                    const XT *win = reinterpret_cast<const XT *>(S.win(w));
+                    sum = row_sum<AT>(k0, k1, [&](int k) { return (int)lc[k]; },
+                                      [&](int c2) { return AT(win[c2]); }, vs);
                 } else {
                     const int32_t *cs = S.cols(w) - (d.a & ~3);
-                    sum = row_sum(k0, k1, [&](int k) { return cs[k]; },
-                                  [&](int c2) { return x[c2]; }, vs);
+                    sum = row_sum<AT>(k0, k1, [&](int k) { return cs[k]; },
+                                      [&](int c2) { return AT(x[c2]); }, vs);
                 }
             }
             epi.row(row, sum, j);
@@ -449,21 +479,22 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
     }
     __syncwarp();  // every lane is done with the stage
     ++pp.consumed;
-    issue_next(P, S, pp, t0, m, limit, pass_end, x);
+    issue_next<VT, XT>(P, S, pp, t0, m, limit, pass_end, vals, x);
     return true;
 }
 
-// Row sums of this CTA's rows with the vector x (16-byte aligned, padded):
-// epi.row(i, sum_k vals[k] * x[colidx[k]], j) is called once per row by the
-// thread that owns it.  RPT > 0 unrolls the warp's tile loop (at most RPT
-// tiles per warp) so that j is a compile-time index into register-resident
-// row state; RPT = 0 loops at run time.  `one_pass` stops the pipeline at the
-// end of the pass (the plain SpMV); otherwise the next pass's first tile is
-// left in flight (matrix part only).  Returns false in every thread of the
-// CTA if a TMA wait ran out (the error is recorded).
-template <int RPT, class Epi>
-__device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe &pp, const double *x,
-                                           Epi &epi, bool one_pass = false) {
+// Row sums of this CTA's rows: epi.row(i, sum_k vals[k] * x[colidx[k]], j)
+// is called once per row by the thread that owns it; VT is the stored value
+// type, XT the vector element type (x 16-byte aligned), AT the accumulation
+// type.  RPT > 0 unrolls the warp's tile loop (at most RPT tiles per warp)
+// so that j is a compile-time index into register-resident row state;
+// RPT = 0 loops at run time.  `one_pass` stops the pipeline at the end of
+// the pass; otherwise the next pass's first tile is left in flight (matrix
+// part only, same value type).  Returns false in every thread of the CTA if
+// a TMA wait ran out (the error is recorded).
+template <int RPT, class VT, class XT, class AT, class Epi>
+__device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe &pp, const VT *vals,
+                                           const XT *x, Epi &epi, bool one_pass = false) {
     const int t0 = P.cta_tile[blockIdx.x], t1 = P.cta_tile[blockIdx.x + 1];
     const int nt = t1 - t0;
     const int w = threadIdx.x >> 5;
@@ -475,18 +506,19 @@ __device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe 
         // windows of tiles whose matrix part was issued during the last pass
         while (pp.win_issued < pp.issued) {
             const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
-            issue_window(P, S, d, w, x);
+            issue_window<XT>(P, S, d, w, x);
             ++pp.win_issued;
         }
-        issue_next(P, S, pp, t0, m, limit, pass_end, x);
+        issue_next<VT, XT>(P, S, pp, t0, m, limit, pass_end, vals, x);
         if (RPT > 0) {
 #pragma unroll
             for (int j = 0; j < (RPT > 0 ? RPT : 1); ++j) {
-                if (j < m && !failed) failed = !warp_tile(P, S, pp, t0, m, limit, pass_end, x, epi, j);
+                if (j < m && !failed)
+                    failed = !warp_tile<VT, XT, AT>(P, S, pp, t0, m, limit, pass_end, vals, x, epi, j);
             }
         } else {
             for (int j = 0; j < m && !failed; ++j)
-                failed = !warp_tile(P, S, pp, t0, m, limit, pass_end, x, epi, j);
+                failed = !warp_tile<VT, XT, AT>(P, S, pp, t0, m, limit, pass_end, vals, x, epi, j);
         }
     }
     if (__syncthreads_or(failed)) {
@@ -500,14 +532,15 @@ __device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe 
 // targets shared memory after the CTA exits.  A prefetched tile whose window
 // was never issued cannot complete its phase, so the window is issued first
 // (from any vector: the data is not used).
-__device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp, const double *any_x) {
+template <class XT>
+__device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp, const XT *any_x) {
     const int w = threadIdx.x >> 5;
     const int t0 = P.cta_tile[blockIdx.x], nt = P.cta_tile[blockIdx.x + 1] - t0;
     const int m = nt > w ? (nt - w + kWarps - 1) / kWarps : 0;
     if (m > 0) {
         while (pp.win_issued < pp.issued) {
             const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
-            issue_window(P, S, d, w, any_x);
+            issue_window<XT>(P, S, d, w, any_x);
             ++pp.win_issued;
         }
         if ((threadIdx.x & 31) == 0) {

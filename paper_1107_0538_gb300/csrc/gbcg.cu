@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "cg_device.cuh"
+#include "lowprec.h"
 #include "plan.h"
 #include "gbcg.h"
 
@@ -186,11 +187,11 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
         double v[3];
         if constexpr (RPT > 0) {
             RegSetup<RPT> epi{R, P.b, p, P.precond};
-            if (!spmv_tiles<RPT>(P, S, pipe, P.x, epi)) goto out;
+            if (!spmv_tiles<RPT, double, double, double>(P, S, pipe, P.vals, P.x, epi)) goto out;
             v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
         } else {
             EpiSetup epi{P.b, P.r, P.z, p, P.dinv, P.precond};
-            if (!spmv_tiles<0>(P, S, pipe, P.x, epi)) goto out;
+            if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, epi)) goto out;
             v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
         }
         block_sum<3>(v, S);
@@ -242,11 +243,11 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
             double pq;
             if constexpr (RPT > 0) {
                 RegIter<RPT> ei{R};
-                if (!spmv_tiles<RPT>(P, S, pipe, p, ei)) goto out;
+                if (!spmv_tiles<RPT, double, double, double>(P, S, pipe, P.vals, p, ei)) goto out;
                 pq = ei.pq;
             } else {
                 EpiIter ei{P.q, p};
-                if (!spmv_tiles<0>(P, S, pipe, p, ei)) goto out;
+                if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, p, ei)) goto out;
                 pq = ei.pq;
             }
             double v1[1] = {pq};
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
                 if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
             }
             EpiTrue et{P.b};
-            if (!spmv_tiles<RPT>(P, S, pipe, P.x, et)) goto out;
+            if (!spmv_tiles<RPT, double, double, double>(P, S, pipe, P.vals, P.x, et)) goto out;
             double v[1] = {et.acc};
             block_sum<1>(v, S);
             publish_partials<1>(P, set, v);
@@ -391,7 +392,185 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
         atomicCAS(&P.st->status, 0, status);
     }
 out:
-    drain(P, S, pipe, p);
+    drain<double>(P, S, pipe, p);
+}
+
+// ---------------------------------------------- mixed-precision solve
+// Iterative refinement: the outer loop keeps x and the residual in FP64 with
+// the FP64 matrix (r = b - A x, stop when ||r|| <= tol ||b||, x += d); each
+// correction d solves A_lo d = r by CG in FP32 (FP32 vectors, FP32 products
+// and per-thread sums) on the low-precision copy of A (FP32 or BF16
+// off-diagonals plus the compensated FP32 diagonal), optionally with Jacobi,
+// until its residual falls by inner_tol.  One persistent launch runs it all.
+struct EpiOuter {       // r = b - A x; inner start r32 = z32/p32, d32 = 0
+    const double *b;
+    float *r32, *z32, *p32, *d32;
+    const float *dinv32;
+    int precond;
+    double rr = 0.0, bb = 0.0;
+    float rz = 0.0f;
+    __device__ __forceinline__ void row(int i, double ax, int) {
+        const double bi = b[i];
+        const double ri = bi - ax;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+        const float rf = (float)ri;
+        r32[i] = rf;
+        const float zf = precond ? dinv32[i] * rf : rf;
+        if (precond) z32[i] = zf;
+        p32[i] = zf;
+        d32[i] = 0.0f;
+        rz = fmaf(rf, zf, rz);
+    }
+};
+
+struct EpiInner {       // q = A_lo p (+ compensated diagonal); sum p . q
+    float *q32;
+    const float *p32;
+    const float *diag;
+    float pq = 0.0f;
+    __device__ __forceinline__ void row(int i, float s, int) {
+        const float pi = p32[i];
+        const float qi = fmaf(diag[i], pi, s);
+        q32[i] = qi;
+        pq = fmaf(pi, qi, pq);
+    }
+};
+
+template <class VT>
+__global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    init_pipeline(S);
+    unsigned int epoch = 0;
+    Pipe pipe;
+    int set = 0;
+    const int tid = threadIdx.x;
+    const int row_lo = P.cta_row[blockIdx.x];
+    const int row_hi = P.cta_row[blockIdx.x + 1];
+    const VT *vlo = nullptr;
+    if constexpr (sizeof(VT) == 4) vlo = reinterpret_cast<const VT *>(P.vals32);
+    else vlo = reinterpret_cast<const VT *>(P.vals16);
+
+    // thread 0's scalar state
+    int status = CG_ENOCONV, inner_total = 0, outer = 0;
+    double rr = 0.0, bb = 0.0, bnorm = 0.0;
+
+    for (int o = 0;; ++o) {
+        // ---- outer residual in FP64 and the start of the inner solve
+        double rho;
+        {
+            EpiOuter eo{P.b, P.r32, P.z32, P.p32, P.d32, P.dinv32, P.precond};
+            if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, eo, true)) goto out;
+            double v[3] = {eo.rr, eo.bb, (double)eo.rz};
+            block_sum<3>(v, S);
+            publish_partials<3>(P, set, v);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double t[3];
+            grid_totals<3>(P, set, t);
+            set ^= 1;
+            if (tid == 0) {
+                rr = t[0];
+                if (o == 0) {
+                    bb = t[1];
+                    bnorm = sqrt(bb);
+                }
+                int go = 0, zero_b = 0;
+                if (!finite_bits(bb) || !finite_bits(rr) || !finite_bits(t[2])) status = CG_ENAN;
+                else if (bnorm == 0.0) { status = CG_OK; zero_b = 1; rr = 0.0; }
+                else if (sqrt(rr) <= P.tol * bnorm) status = CG_OK;
+                else if (o == P.max_outer || inner_total >= P.maxit) status = CG_ENOCONV;
+                else if (!(t[2] > 0.0)) status = CG_EBREAKDOWN;
+                else go = 1;
+                S.bcast[0] = t[2];                       // rho of the inner start
+                S.bcast[1] = P.inner_tol * sqrt(t[0]) ;  // inner target on ||r32||
+                S.ctl[kCtlRun] = go;
+                S.ctl[kCtlZeroB] = zero_b;
+            }
+            __syncthreads();
+            if (S.ctl[kCtlZeroB])
+                for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] = 0.0;
+            if (!S.ctl[kCtlRun]) break;
+            rho = S.bcast[0];  // only thread 0 uses rho; the others never read it again
+        }
+
+        // ---- inner CG in FP32 on A_lo d = r
+        for (int k = 1;; ++k) {
+            EpiInner ei{P.q32, P.p32, P.diag_lo};
+            if (!spmv_tiles<0, VT, float, float>(P, S, pipe, vlo, P.p32, ei, true)) goto out;
+            double v1[1] = {(double)ei.pq};
+            block_sum<1>(v1, S);
+            publish_partials<1>(P, set, v1);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double sg[1];
+            grid_totals<1>(P, set, sg);
+            set ^= 1;
+            if (tid == 0) {
+                int go = 1;
+                if (!finite_bits(sg[0]) || !(sg[0] > 0.0)) go = 0;  // inner breakdown: keep d
+                S.bcast[2] = go ? rho / sg[0] : 0.0;
+                S.ctl[kCtlRun] = go;
+                if (!go && k == 1) status = finite_bits(sg[0]) ? CG_EBREAKDOWN : CG_ENAN;
+            }
+            __syncthreads();
+            if (!S.ctl[kCtlRun]) break;
+            const float alpha = (float)S.bcast[2];
+            float prr = 0.0f, prz = 0.0f;
+            for (int i = row_lo + tid; i < row_hi; i += kThreads) {
+                P.d32[i] = fmaf(alpha, P.p32[i], P.d32[i]);
+                const float ri = fmaf(-alpha, P.q32[i], P.r32[i]);
+                P.r32[i] = ri;
+                prr = fmaf(ri, ri, prr);
+                if (P.precond) {
+                    const float zi = P.dinv32[i] * ri;
+                    P.z32[i] = zi;
+                    prz = fmaf(ri, zi, prz);
+                }
+            }
+            double v2[2] = {(double)prr, (double)(P.precond ? prz : prr)};
+            block_sum<2>(v2, S);
+            publish_partials<2>(P, set, v2);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double t2[2];
+            grid_totals<2>(P, set, t2);
+            set ^= 1;
+            if (tid == 0) {
+                ++inner_total;
+                int go = 0;
+                const double rin = t2[0], rho_new = t2[1];
+                if (!finite_bits(rin) || !finite_bits(rho_new) || !(rho_new > 0.0)) go = 0;
+                else if (sqrt(rin) <= S.bcast[1]) go = 0;                 // inner target met
+                else if (k >= P.max_inner || inner_total >= P.maxit) go = 0;
+                else go = 1;
+                if (go) {
+                    S.bcast[3] = rho_new / rho;
+                    rho = rho_new;
+                }
+                S.ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!S.ctl[kCtlRun]) break;
+            const float beta = (float)S.bcast[3];
+            for (int i = row_lo + tid; i < row_hi; i += kThreads)
+                P.p32[i] = fmaf(beta, P.p32[i], P.precond ? P.z32[i] : P.r32[i]);
+            if (!grid_barrier(P, epoch, S)) goto out;
+        }
+        // ---- x += d in FP64
+        for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] += (double)P.d32[i];
+        if (tid == 0) outer = o + 1;
+        if (!grid_barrier(P, epoch, S)) goto out;
+    }
+
+    if (blockIdx.x == 0 && tid == 0) {
+        P.st->iters = inner_total;
+        P.st->outer = outer;
+        P.st->rr = rr;
+        P.st->bb = bb;
+        P.st->true_rr = rr;  // the outer residual is the true FP64 residual
+        atomicCAS(&P.st->status, 0, status);
+    }
+out:
+    drain<float>(P, S, pipe, P.p32);
 }
 
 // ------------------------------------------------------- plain SpMV kernel
@@ -401,8 +580,8 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
     init_pipeline(S);
     Pipe pipe;
     EpiStore epi{P.q};
-    (void)spmv_tiles<0>(P, S, pipe, P.x, epi, true);
-    drain(P, S, pipe, P.x);
+    (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, epi, true);
+    drain<double>(P, S, pipe, P.x);
 }
 
 using SolveKernel = void (*)(Params);
@@ -438,6 +617,10 @@ struct cg_handle {
     int4 *tiles = nullptr, *segs = nullptr;
     uint16_t *lcol = nullptr;
     int window_tiles = 0;
+    // mixed precision
+    float *vals32 = nullptr, *diag_lo = nullptr, *dinv32 = nullptr;
+    uint16_t *vals16 = nullptr;
+    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
     double *vals = nullptr, *dinv = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
     double *partials = nullptr, *b_dev = nullptr, *x_dev = nullptr;
@@ -497,6 +680,18 @@ Params base_params(const cg_handle *h) {
     P.colidx = h->colidx;
     P.vals = h->vals;
     P.tiles = h->tiles;
+    P.vals32 = h->vals32;
+    P.vals16 = reinterpret_cast<const __nv_bfloat16 *>(h->vals16);
+    P.diag_lo = h->diag_lo;
+    P.dinv32 = h->dinv32;
+    P.r32 = h->r32;
+    P.z32 = h->z32;
+    P.p32 = h->p32;
+    P.q32 = h->q32;
+    P.d32 = h->d32;
+    P.inner_tol = h->opts.inner_tol;
+    P.max_outer = h->opts.max_outer;
+    P.max_inner = h->opts.max_inner > 0 ? h->opts.max_inner : h->n;
     P.lcol = h->lcol;
     P.segs = h->segs;
     P.cta_tile = h->cta_tile;
@@ -530,7 +725,10 @@ int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess) {
         void *args[] = {&P};
-        e = cudaLaunchCooperativeKernel((const void *)h->kernel, dim3(h->ctas), dim3(kThreads),
+        const void *kern = (const void *)h->kernel;
+        if (h->opts.inner_values == CG_VALUES_FP32) kern = (const void *)cg_ir_kernel<float>;
+        if (h->opts.inner_values == CG_VALUES_BF16) kern = (const void *)cg_ir_kernel<__nv_bfloat16>;
+        e = cudaLaunchCooperativeKernel(kern, dim3(h->ctas), dim3(kThreads),
                                         args, (size_t)kSmemBytes, h->stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
@@ -553,6 +751,7 @@ int finish_solve(cg_handle *h, cg_info *info) {
     out.relres_true = s.true_rr < 0.0 ? -1.0 : (bnorm > 0.0 ? std::sqrt(s.true_rr) / bnorm : 0.0);
     out.kernel_ms = ms;
     out.launches = 1;
+    out.outer = s.outer;
     if (info) *info = out;
     return s.status;
 }
@@ -586,6 +785,10 @@ int cg_opts_default(cg_opts *opts) {
     opts->grid_ctas = 0;
     opts->debug_phantom_arrivals = 0;
     opts->vectors_in_memory = 0;
+    opts->inner_values = CG_VALUES_FP64;
+    opts->inner_tol = 0.0;
+    opts->max_outer = 50;
+    opts->max_inner = 0;
     return CG_OK;
 }
 
@@ -619,6 +822,12 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     if (opts.grid_ctas < 0 || opts.debug_phantom_arrivals < 0 || opts.debug_phantom_arrivals > 1024)
         return CG_EINVAL;
     if (opts.vectors_in_memory != 0 && opts.vectors_in_memory != 1) return CG_EINVAL;
+    if (opts.inner_values != CG_VALUES_FP64 && opts.inner_values != CG_VALUES_FP32 &&
+        opts.inner_values != CG_VALUES_BF16)
+        return CG_EINVAL;
+    if (opts.inner_tol == 0.0) opts.inner_tol = opts.inner_values == CG_VALUES_BF16 ? 1e-2 : 1e-3;
+    if (!(opts.inner_tol > 0.0 && opts.inner_tol < 1.0) || opts.max_outer < 1 || opts.max_inner < 0)
+        return CG_EINVAL;
     const int32_t n = A->n;
     const int64_t nnz = A->nnz;
     if (n < 0 || nnz < 0 || nnz > (int64_t)INT32_MAX - 64) return CG_EINVAL;
@@ -695,7 +904,11 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
             return fail(CG_ECUDA);
     }
     if (cudaFuncSetAttribute((const void *)spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBytes) != cudaSuccess)
+                             kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)cg_ir_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)cg_ir_kernel<__nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
         return fail(CG_ECUDA);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(4), kThreads, kSmemBytes) !=
             cudaSuccess ||
@@ -754,6 +967,29 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     } else {
         h->z = h->r;
     }
+    InnerMatrix inner;
+    const bool mixed = opts.inner_values != CG_VALUES_FP64;
+    if (mixed) {
+        inner = build_inner(n, rowptr, colidx, vals, opts.inner_values == CG_VALUES_FP32 ? 1 : 2);
+        if (opts.precond == CG_PRECOND_JACOBI)
+            for (int32_t i = 0; i < n; ++i)
+                if (!(inner.diag[i] > 0.0f) || !std::isfinite(inner.diag[i])) return fail(CG_EINVAL);
+        if (opts.inner_values == CG_VALUES_FP32) {
+            if ((rc = dev_alloc(h, &h->vals32, (size_t)nnz + pad))) return fail(rc);
+        } else {
+            if ((rc = dev_alloc(h, &h->vals16, (size_t)nnz + 2 * pad))) return fail(rc);
+        }
+        if ((rc = dev_alloc(h, &h->diag_lo, (size_t)n)) || (rc = dev_alloc(h, &h->r32, (size_t)n)) ||
+            (rc = dev_alloc(h, &h->p32, (size_t)n + pad)) || (rc = dev_alloc(h, &h->q32, (size_t)n)) ||
+            (rc = dev_alloc(h, &h->d32, (size_t)n)))
+            return fail(rc);
+        if (opts.precond == CG_PRECOND_JACOBI) {
+            if ((rc = dev_alloc(h, &h->z32, (size_t)n)) || (rc = dev_alloc(h, &h->dinv32, (size_t)n)))
+                return fail(rc);
+        } else {
+            h->z32 = h->r32;
+        }
+    }
     if (cudaMallocHost(&h->st_host, sizeof(DevStatus)) != cudaSuccess) return fail(CG_ENOMEM);
     if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
         return fail(CG_ECUDA);
@@ -781,6 +1017,25 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         e = cudaMemcpy(h->cta_row, cta_row.data(), sizeof(int32_t) * cta_row.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && opts.precond == CG_PRECOND_JACOBI && n > 0)
         e = cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && mixed && n > 0) {
+        if (opts.inner_values == CG_VALUES_FP32) {
+            e = cudaMemset(h->vals32, 0, sizeof(float) * (nnz + pad));
+            if (e == cudaSuccess && nnz > 0)
+                e = cudaMemcpy(h->vals32, inner.vals32.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemset(h->vals16, 0, sizeof(uint16_t) * (nnz + 2 * pad));
+            if (e == cudaSuccess && nnz > 0)
+                e = cudaMemcpy(h->vals16, inner.vals16.data(), sizeof(uint16_t) * nnz, cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->diag_lo, inner.diag.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(h->p32, 0, sizeof(float) * (n + pad));
+        if (e == cudaSuccess && opts.precond == CG_PRECOND_JACOBI) {
+            std::vector<float> di(n);
+            for (int32_t i = 0; i < n; ++i) di[i] = 1.0f / inner.diag[i];
+            e = cudaMemcpy(h->dinv32, di.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) return fail(cuda_fail(e));
     *out = h;
     return CG_OK;

@@ -21,8 +21,10 @@ namespace gbcg {
 constexpr int kThreads = 512;                  // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kTileRows = 32;                  // rows per warp tile (one per lane)
-constexpr int kTileNnz = 896;                  // stored entries per warp tile
-constexpr int kWinMax = 384;                   // doubles of x-window per tile
+constexpr int kTileNnz = 864;                  // stored entries per warp tile (32 rows x 27)
+constexpr int kWinMax = 448;                   // elements of x-window per tile
+constexpr int kSegAlign = 4;                   // window segments start/end on 4 elements:
+                                               // 16-byte TMA alignment for FP64 and FP32 vectors
 constexpr int kSegMax = 32;                    // window segments per tile (one per lane)
 constexpr int kBatch = 9;                      // loads in flight per thread
 constexpr int kValsStage = kTileNnz + 8;       // doubles per stage (alignment slack)
@@ -44,7 +46,7 @@ constexpr int kTileGather = 1;   // 32-bit global columns, gathers from global m
 constexpr int kTileLong = 2;     // one row longer than kTileNnz, read from global memory
 
 // One row tile: rows [r0, r1) holding entries [a, e); window segments
-// segs[seg0 .. seg0 + nseg) whose TMA copies deliver wtx doubles in total.
+// segs[seg0 .. seg0 + nseg) whose TMA copies deliver wtx elements in total.
 struct TileDesc {
     int32_t r0, r1, a, e;
     int32_t seg0, nseg, wtx, kind;

@@ -41,11 +41,13 @@ std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, i
 }
 
 // x-window of one tile: the distinct columns grouped into runs (gaps of up
-// to kGap unused columns are bridged), each run widened to 16-byte (2
-// double) boundaries; a run that would end past the vector's last column
-// (n odd) stops short and names that column as its tail.  Windowed when the
-// runs fit kSegMax lanes and kWinMax doubles; each entry then stores its
-// 16-bit offset in the window.
+// to kGap unused columns are bridged), each run widened to kSegAlign-element
+// boundaries so that its TMA copy is 16-byte aligned for FP64 and FP32
+// vectors alike.  A run that would end past the vector's last column stops
+// at the last aligned column n & ~3; the 1 to 3 columns after it (its tail)
+// are stored into the window by threads.  Windowed when the runs fit kSegMax
+// lanes and kWinMax elements; each entry then stores its 16-bit offset in
+// the window.
 constexpr int kGap = 4;
 
 struct TilePlan {
@@ -77,8 +79,8 @@ TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::
             runs.clear();
             int first = cols[0], last = cols[0];
             auto flush = [&]() {
-                const int gs = first & ~1;
-                int ge = (last + 2) & ~1;  // exclusive, even
+                const int gs = first & ~(kSegAlign - 1);
+                int ge = (last + kSegAlign) & ~(kSegAlign - 1);  // exclusive, aligned
                 if (!runs.empty() && gs <= runs.back().y) {
                     runs.back().y = std::max(runs.back().y, ge);
                 } else {
@@ -101,9 +103,9 @@ TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::
                 I4 sg;
                 sg.x = rr.x;
                 sg.y = woff;
-                if (rr.y > n) {  // runs to n + 1: n odd, stop before the last column
-                    sg.z = (n - 1) - rr.x;
-                    sg.w = n - 1;
+                if (rr.y > n) {  // runs past the vector: copy up to n & ~3, store the tail
+                    sg.z = (n & ~(kSegAlign - 1)) - rr.x;
+                    sg.w = n & ~(kSegAlign - 1);
                 } else {
                     sg.z = rr.y - rr.x;
                     sg.w = -1;
@@ -204,12 +206,14 @@ inline std::string check_plan(int32_t n, const std::vector<int32_t> &rowptr,
         int tx = 0, slots_end = 0;
         for (int i = 0; i < nseg; ++i) {
             const I4 sg = tp.segs[seg0 + i];
-            if (sg.x < 0 || (sg.x & 1) || (sg.y & 1) || sg.z < 0 || (sg.z & 1)) return err(t, "segment alignment");
+            const int al = kSegAlign - 1;
+            if (sg.x < 0 || (sg.x & al) || (sg.y & al) || sg.z < 0 || (sg.z & al)) return err(t, "segment alignment");
             if (sg.y != slots_end) return err(t, "segment offsets");
             if (sg.x + sg.z > n) return err(t, "segment past the vector");
-            if (sg.w >= 0 && (sg.w != sg.x + sg.z || sg.w != n - 1)) return err(t, "tail column");
+            if (sg.w >= 0 && (sg.w != sg.x + sg.z || sg.w != (n & ~al) || n - sg.w < 1 || n - sg.w > al))
+                return err(t, "tail columns");
             if (i > 0 && sg.x < tp.segs[seg0 + i - 1].x + tp.segs[seg0 + i - 1].z) return err(t, "segment order");
-            slots_end = sg.y + sg.z + (sg.w >= 0 ? 2 : 0);
+            slots_end = sg.y + sg.z + (sg.w >= 0 ? kSegAlign : 0);
             tx += sg.z;
         }
         if (tx != wtx || slots_end > kWinMax) return err(t, "window size");
@@ -219,7 +223,9 @@ inline std::string check_plan(int32_t n, const std::vector<int32_t> &rowptr,
             int i = nseg - 1;
             while (i > 0 && tp.segs[seg0 + i].y > lc) --i;
             const I4 sg = tp.segs[seg0 + i];
-            const int col = lc - sg.y < sg.z ? sg.x + (lc - sg.y) : (lc - sg.y == sg.z ? sg.w : -2);
+            int col = -2;
+            if (lc - sg.y < sg.z) col = sg.x + (lc - sg.y);
+            else if (sg.w >= 0 && lc - sg.y - sg.z < n - sg.w) col = sg.w + (lc - sg.y - sg.z);
             if (col != colidx[k]) return err(t, "local column maps to the wrong column");
         }
     }

@@ -24,6 +24,7 @@ CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA = 0, 1, 2, 3
 CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT = 4, 5, 6, 7
 CG_MEM_HOST, CG_MEM_DEVICE = 0, 1
 CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
@@ -44,16 +45,18 @@ class cg_csr(ctypes.Structure):
 class cg_opts(ctypes.Structure):
     _fields_ = [("precond", ctypes.c_int32), ("true_residual", ctypes.c_int32),
                 ("wait_limit_s", ctypes.c_double), ("grid_ctas", ctypes.c_int32),
-                ("debug_phantom_arrivals", ctypes.c_int32), ("vectors_in_memory", ctypes.c_int32)]
+                ("debug_phantom_arrivals", ctypes.c_int32), ("vectors_in_memory", ctypes.c_int32),
+                ("inner_values", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32)]
 
 
 class cg_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
                 ("relres_true", ctypes.c_double), ("kernel_ms", ctypes.c_double),
-                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("outer", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class cg_plan(ctypes.Structure):
@@ -182,7 +185,8 @@ class Solver:
 
     def __init__(self, A, precond: int = CG_PRECOND_NONE, true_residual: bool = True,
                  wait_limit_s: float = 5.0, grid_ctas: int = 0, debug_phantom_arrivals: int = 0,
-                 vectors_in_memory: bool = False, stream=None):
+                 vectors_in_memory: bool = False, inner_values: int = CG_VALUES_FP64,
+                 inner_tol: float = 0.0, max_outer: int = 50, max_inner: int = 0, stream=None):
         import torch
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -193,6 +197,10 @@ class Solver:
         o.grid_ctas = grid_ctas
         o.debug_phantom_arrivals = debug_phantom_arrivals
         o.vectors_in_memory = 1 if vectors_in_memory else 0
+        o.inner_values = inner_values
+        o.inner_tol = inner_tol
+        o.max_outer = max_outer
+        o.max_inner = max_inner
         csr, self._keep = host_csr(A)
         rc, self.h = cg_create(csr, o, self.stream.cuda_stream)
         if rc != CG_OK:

@@ -55,8 +55,9 @@ int main(void) {
   F(cg_csr, n) F(cg_csr, nnz) F(cg_csr, rowptr) F(cg_csr, colidx) F(cg_csr, vals) F(cg_csr, mem)
   F(cg_opts, precond) F(cg_opts, true_residual) F(cg_opts, wait_limit_s) F(cg_opts, grid_ctas)
   F(cg_opts, debug_phantom_arrivals) F(cg_opts, vectors_in_memory)
+  F(cg_opts, inner_values) F(cg_opts, inner_tol) F(cg_opts, max_outer) F(cg_opts, max_inner)
   F(cg_info, iters) F(cg_info, status) F(cg_info, relres) F(cg_info, relres_true)
-  F(cg_info, kernel_ms) F(cg_info, launches) F(cg_info, reserved)
+  F(cg_info, kernel_ms) F(cg_info, launches) F(cg_info, outer)
   F(cg_plan, n) F(cg_plan, nnz) F(cg_plan, ctas) F(cg_plan, threads) F(cg_plan, tiles)
   F(cg_plan, tile_nnz) F(cg_plan, stages) F(cg_plan, smem_bytes) F(cg_plan, lanes_per_row)
   F(cg_plan, l2_evict_first) F(cg_plan, reg_rows) F(cg_plan, window_tiles) F(cg_plan, device_bytes)
@@ -125,7 +126,8 @@ def test_bad_options_rejected_without_gpu():
     c, keep = gbcg.host_csr(A)
     for field, value in [("precond", 3), ("wait_limit_s", 0.0), ("wait_limit_s", float("nan")),
                          ("grid_ctas", -1), ("debug_phantom_arrivals", -2),
-                         ("vectors_in_memory", 2)]:
+                         ("vectors_in_memory", 2), ("inner_values", 3), ("inner_tol", 1.5),
+                         ("inner_tol", -1.0), ("max_outer", 0), ("max_inner", -1)]:
         o = gbcg.cg_opts_default()
         setattr(o, field, value)
         rc, h = gbcg.cg_create(c, o, None)
