@@ -202,6 +202,36 @@ void cg_destroy(cg_handle *h);
 /* Static description of a status code ("unknown status" for other values). */
 const char *cg_strerror(int code);
 
+/*
+ * Largest n that cg_solve_noalloc accepts (its fixed workspace holds three
+ * vectors of this length: 6 MiB, held by every GPU that loads the library
+ * until the process exits).
+ */
+#define CG_NOALLOC_MAX_N 262144
+
+/*
+ * FP64 CG without any allocation, for callers that cannot allocate: code
+ * running while a stream is captured into a graph (cudaMalloc is not a
+ * capturable operation and synchronizes the device), code inside a framework
+ * whose caching allocator owns all device memory, real-time loops that cannot
+ * afford an allocation's synchronization.  The paper has no counterpart; it
+ * computes what cg_solve computes with CG_PRECOND_NONE (same recurrence, stop
+ * test and status codes) from the caller's arrays: A must be CG_MEM_DEVICE
+ * (rowptr, colidx, vals on the current device), b and x are device vectors
+ * (x: in x0, out the last iterate), stream is a cudaStream_t.  Its workspace
+ * is one fixed __device__ array shared by all calls: each call clears what
+ * must start at zero, but calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Synchronous.  Returns CG_EINVAL for n >
+ * CG_NOALLOC_MAX_N, host-resident arrays, NULL vectors or b == x, and for a
+ * malformed matrix found by the kernel (row range or column out of bounds;
+ * such entries are never read); otherwise as cg_solve.  info->kernel_ms is 0
+ * and relres_true is -1 (no events, no extra SpMV).
+ */
+int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit,
+                     void *stream, cg_info *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,8 @@ CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
-           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror")
+           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_solve_noalloc")
+CG_NOALLOC_MAX_N = 262144
 
 
 class GbcgError(RuntimeError):
@@ -104,6 +105,9 @@ def lib() -> ctypes.CDLL:
             L.cg_destroy.restype = None
             L.cg_strerror.argtypes = [ctypes.c_int]
             L.cg_strerror.restype = ctypes.c_char_p
+            L.cg_solve_noalloc.argtypes = [ctypes.POINTER(cg_csr), vp, vp, dbl, i32, vp,
+                                           ctypes.POINTER(cg_info)]
+            L.cg_solve_noalloc.restype = ctypes.c_int
             _LIB = L
     return _LIB
 
@@ -162,6 +166,15 @@ def cg_destroy(h: int | None) -> None:
 
 def cg_strerror(code: int) -> str:
     return lib().cg_strerror(int(code)).decode()
+
+
+def cg_solve_noalloc(A: cg_csr, b_ptr: int, x_ptr: int, tol: float, maxit: int,
+                     stream: int | None) -> tuple[int, cg_info]:
+    """The allocation-free solve (device CSR and vectors; see include/gbcg.h)."""
+    info = cg_info()
+    rc = lib().cg_solve_noalloc(ctypes.byref(A), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                                float(tol), int(maxit), ctypes.c_void_p(stream or 0), ctypes.byref(info))
+    return rc, info
 
 
 # ------------------------------------------------------------ convenience

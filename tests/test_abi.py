@@ -164,3 +164,12 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "cg_oracle" not in text and "liboracle" not in text, f
+
+
+def test_noalloc_rejects_sizes_beyond_its_workspace_without_gpu():
+    c = gbcg.cg_csr(gbcg.CG_NOALLOC_MAX_N + 1, 0, 1, 1, 1, gbcg.CG_MEM_DEVICE)
+    rc, _ = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
+    assert rc == gbcg.CG_EINVAL
+    c = gbcg.cg_csr(10, 0, 1, 1, 1, gbcg.CG_MEM_HOST)  # host arrays are not accepted
+    rc, _ = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
+    assert rc == gbcg.CG_EINVAL
