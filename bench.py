@@ -77,8 +77,9 @@ def measured_peaks() -> dict:
 
 
 def ncu_traffic(kernel: str) -> dict | None:
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
-    summary was taken on the current kernel source (hash match), else None."""
+    """DRAM bytes per launch of a kernel from the committed ncu capture summary
+    (profiles/ncu_traffic.txt), if it was taken on the current kernel source
+    (digest match), else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
@@ -90,8 +91,8 @@ def ncu_traffic(kernel: str) -> dict | None:
     digest = h.hexdigest()[:16]
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and parts[0] == kernel and parts[1] == digest:
-            return {"dram_bytes": float(parts[2]), "units": float(parts[3])}
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return {"dram_bytes_per_launch": float(parts[2])}
     return None
 
 
@@ -261,7 +262,7 @@ def run_gbcg(args) -> None:
         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
         "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-        "traffic": (round(tr["dram_bytes"] / tr["units"] * iters) if tr else None),
+        "traffic": (round(tr["dram_bytes_per_launch"]) if tr else None),
         "algorithmic_flops_per_launch": iters * fpi,
         "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
@@ -354,7 +355,7 @@ def run_gbcg(args) -> None:
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
             "algorithmic_bytes": sb,
             "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),
-            "traffic": (round(trs["dram_bytes"] / trs["units"] * big.A.nnz) if trs else None),
+            "traffic": (round(trs["dram_bytes_per_launch"]) if trs else None),
         }
         bs.close()
         line["gpu_launches"] += 0  # extras are outside the timed region
