@@ -202,6 +202,81 @@ void cg_destroy(cg_handle *h);
 /* Static description of a status code ("unknown status" for other values). */
 const char *cg_strerror(int code);
 
+/* ---- batched solves ---------------------------------------------------- */
+
+/* Result of one (system, right-hand side) pair of a batched solve. */
+typedef struct {
+    int32_t iters;           /* inner iterations, all refinement steps           */
+    int32_t outer;           /* refinement steps applied                         */
+    int32_t status;          /* CG_OK, CG_ENOCONV, CG_EBREAKDOWN or CG_ENAN      */
+    int32_t reserved;
+    double relres;           /* ||b - A x||_2 / ||b||_2 (FP64) at the last check  */
+} cg_batch_result;
+
+/* What cg_batch_tune chose. */
+typedef struct {
+    double inner_tol;        /* inner tolerance of the fastest trial             */
+    int32_t gather_tiles;    /* 1: tiles gather x from memory instead of staging
+                                x-windows                                       */
+    int32_t trials;
+    double best_ms;          /* device time of the fastest trial                 */
+} cg_batch_tuning;
+
+typedef struct cg_batch cg_batch;
+
+/*
+ * Many independent SPD systems (nsys >= 1, each a cg_csr as for cg_create,
+ * host or device arrays) solved together: the batched time stepping of an
+ * FEM model, each step a new right-hand side (Section IV solves one such
+ * system; the paper has no batched form).  The systems are stored as one
+ * block-diagonal matrix whose row tiles never cross a system.  Every (system,
+ * right-hand side) pair runs the mixed-precision refinement of cg_solve
+ * (opts->inner_values FP32 or BF16; FP64 is taken as FP32; precond applies
+ * to the inner CG) and all pairs advance in lockstep inside one persistent
+ * cooperative kernel; tiles of finished systems are skipped.  A CTA may
+ * hold tiles of at most 64 systems (CG_EINVAL otherwise).  Synchronous.
+ */
+int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts, void *stream,
+                    cg_batch **out);
+
+/*
+ * Enqueues a batched solve on the handle's stream and returns (no
+ * synchronization; only stream-ordered copies, memsets and one cooperative
+ * kernel launch).  B and X are device arrays of nrhs (1..4) columns over the
+ * concatenated systems: column r of system s starts at
+ * r * N + (rows of systems 0..s-1), N the total row count; X holds x0 and
+ * receives the solutions.  The stop test per pair is the true FP64 residual
+ * ||b - A x|| <= tol ||b|| (squares compared); maxit caps each pair's inner
+ * iterations (<= 0: N).  Read the per-pair results with cg_batch_results
+ * once the stream has passed this work.
+ */
+int cg_batch_enqueue(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol, int32_t maxit);
+
+/*
+ * Copies the per-pair results of the last enqueued solve to results
+ * (nsys x nrhs, system-major; may be NULL) after synchronizing the stream.
+ * Returns CG_OK if every pair converged, else the first failing pair's
+ * status, or CG_ETIMEOUT if a bounded device wait ran out.
+ */
+int cg_batch_results(cg_batch *h, cg_batch_result *results);
+
+/* cg_batch_enqueue + cg_batch_results; kernel_ms (may be NULL) receives the
+ * device time of the enqueued work (CUDA events). */
+int cg_batch_solve(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol, int32_t maxit,
+                   cg_batch_result *results, double *kernel_ms);
+
+/*
+ * Autotuner: times full solves of B (x0 from X, X left unchanged) for each
+ * inner tolerance in {1e-2, 3e-3, 1e-3, 1e-4} (BF16: >= 1e-3) with staged
+ * x-windows and with gather tiles, keeps the fastest converged choice for
+ * later solves and reports it in *choice (may be NULL).
+ */
+int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol,
+                  cg_batch_tuning *choice);
+
+/* Frees the batch handle (NULL is a no-op). */
+void cg_batch_destroy(cg_batch *h);
+
 /*
  * Largest n that cg_solve_noalloc accepts (its fixed workspace holds three
  * vectors of this length: 6 MiB, held by every GPU that loads the library

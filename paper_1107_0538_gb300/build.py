@@ -2,7 +2,7 @@
 
     python -m paper_1107_0538_gb300.build [-v]
 
-Two translation units, one -gencode, static CUDA runtime; the result sits next
+Three translation units, one -gencode, static CUDA runtime; the result sits next
 to this file as libgbcg.so and is loaded by ``gbcg.lib()``.
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ import sys
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
-SOURCES = [os.path.join(_HERE, "csrc", "gbcg.cu"), os.path.join(_HERE, "csrc", "noalloc.cu")]
+SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gbcg.cu", "noalloc.cu", "batch.cu")]
 DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("cg_device.cuh", "layout.h", "plan.h")] + [
     os.path.join(ROOT, "include", "gbcg.h")]
 OUT = os.path.join(_HERE, "libgbcg.so")

@@ -171,18 +171,22 @@ struct Smem {
     double *red;            // kThreads doubles: block-sum transpose
     double *bcast;          // 8 doubles: scalars broadcast by thread 0
     int *ctl;               // 16 ints: decisions broadcast by thread 0
-    __device__ __forceinline__ double *vals(int s) const {
-        return reinterpret_cast<double *>(stage + s * kStageBytes);
+    __device__ __forceinline__ unsigned char *base(int s) const { return stage + s * kStageBytes; }
+    template <class VT, class XT>
+    __device__ __forceinline__ VT *vals(int s) const {
+        return reinterpret_cast<VT *>(base(s) + StageLayout<sizeof(VT), sizeof(XT)>::vals_off);
     }
+    template <class VT, class XT>
     __device__ __forceinline__ int32_t *cols(int s) const {
-        return reinterpret_cast<int32_t *>(stage + s * kStageBytes + kValsStage * 8);
+        return reinterpret_cast<int32_t *>(base(s) + StageLayout<sizeof(VT), sizeof(XT)>::cols_off);
     }
+    template <class VT, class XT>
     __device__ __forceinline__ int32_t *rptr(int s) const {
-        return reinterpret_cast<int32_t *>(stage + s * kStageBytes + kValsStage * 8 + kColsStage * 4);
+        return reinterpret_cast<int32_t *>(base(s) + StageLayout<sizeof(VT), sizeof(XT)>::rptr_off);
     }
-    __device__ __forceinline__ double *win(int s) const {
-        return reinterpret_cast<double *>(stage + s * kStageBytes + kValsStage * 8 + kColsStage * 4 +
-                                          kRptrStage * 4);
+    template <class VT, class XT>
+    __device__ __forceinline__ XT *win(int s) const {
+        return reinterpret_cast<XT *>(base(s) + StageLayout<sizeof(VT), sizeof(XT)>::win_off);
     }
 };
 
@@ -355,35 +359,34 @@ __device__ __forceinline__ void issue_matrix(const Params &P, const Smem &S, con
     const uint32_t wbytes = (uint32_t)d.wtx * (uint32_t)sizeof(XT);
     mbar_arrive_expect_tx(&S.mbar[s], (d.e > d.a ? vbytes + cbytes : 0u) + rbytes + wbytes);
     if (d.e > d.a) {
-        tma_load_1d(S.vals(s), vals + va, vbytes, &S.mbar[s], P.evict_first != 0);
-        tma_load_1d(S.cols(s), csrc, cbytes, &S.mbar[s], P.evict_first != 0);
+        tma_load_1d(S.vals<VT, XT>(s), vals + va, vbytes, &S.mbar[s], P.evict_first != 0);
+        tma_load_1d(S.cols<VT, XT>(s), csrc, cbytes, &S.mbar[s], P.evict_first != 0);
     }
-    tma_load_1d(S.rptr(s), P.rowptr + ra, rbytes, &S.mbar[s], false);
+    tma_load_1d(S.rptr<VT, XT>(s), P.rowptr + ra, rbytes, &S.mbar[s], false);
 }
 
 // Window part of a windowed tile into stage s: lane l copies segment l of
 // the vector x (16-byte aligned).
-template <class XT>
+template <class VT, class XT>
 __device__ __forceinline__ void issue_window(const Params &P, const Smem &S, const TileDesc &d, int s,
                                              const XT *x) {
     const int lane = threadIdx.x & 31;
     if (d.kind != kTileWindow || lane >= d.nseg) return;
     const int4 sg = __ldg(P.segs + d.seg0 + lane);
     if (sg.z > 0)
-        tma_load_1d(reinterpret_cast<XT *>(S.win(s)) + sg.y, x + sg.x, (uint32_t)sg.z * (uint32_t)sizeof(XT),
-                    &S.mbar[s], false);
+        tma_load_1d(S.win<VT, XT>(s) + sg.y, x + sg.x, (uint32_t)sg.z * (uint32_t)sizeof(XT), &S.mbar[s], false);
 }
 
 // A segment running past the vector's end stops at column n & ~3; its lane
 // stores the 1 to 3 columns after that into the window slots that follow.
-template <class XT>
+template <class VT, class XT>
 __device__ __forceinline__ void store_tail(const Params &P, const Smem &S, const TileDesc &d, int s,
                                            const XT *x) {
     const int lane = threadIdx.x & 31;
     if (d.kind != kTileWindow || lane >= d.nseg) return;
     const int4 sg = __ldg(P.segs + d.seg0 + lane);
     if (sg.w >= 0) {
-        XT *win = reinterpret_cast<XT *>(S.win(s));
+        XT *win = S.win<VT, XT>(s);
         for (int c = sg.w; c < P.n; ++c) win[sg.y + sg.z + (c - sg.w)] = x[c];
     }
 }
@@ -401,7 +404,7 @@ __device__ __forceinline__ void issue_next(const Params &P, const Smem &S, Pipe 
         if ((threadIdx.x & 31) == 0) issue_matrix<VT, XT>(P, S, d, w, vals);
         __syncwarp();
         if (pp.issued < pass_end) {  // same pass: the vector is final, load the window now
-            issue_window<XT>(P, S, d, w, x);
+            issue_window<VT, XT>(P, S, d, w, x);
             ++pp.win_issued;
         }
         ++pp.issued;
@@ -443,7 +446,7 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t c = pp.consumed;
     const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(c % (uint32_t)m));
-    store_tail<XT>(P, S, d, w, x);  // nobody reads the stage before the wait below
+    store_tail<VT, XT>(P, S, d, w, x);  // nobody reads the stage before the wait below
     const bool got = mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns);
     if (__any_sync(0xffffffffu, !got)) return false;
     __syncwarp();
@@ -456,20 +459,20 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
         for (int mm = 16; mm >= 1; mm >>= 1) part += __shfl_xor_sync(0xffffffffu, part, mm);
         if (lane == 0) epi.row(d.r0, part, j);
     } else {
-        const VT *vs = reinterpret_cast<const VT *>(S.vals(w)) - (d.a & ~(16 / (int)sizeof(VT) - 1));
-        const int32_t *rs = S.rptr(w) - (d.r0 & ~3);
+        const VT *vs = S.vals<VT, XT>(w) - (d.a & ~(16 / (int)sizeof(VT) - 1));
+        const int32_t *rs = S.rptr<VT, XT>(w) - (d.r0 & ~3);
         const int row = d.r0 + lane;
         if (row < d.r1) {
             const int k0 = rs[row], k1 = rs[row + 1];
             AT sum = AT(0);
             if (k1 > k0) {
                 if (d.kind == kTileWindow) {
-                    const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols(w)) - (d.a & ~7);
-                    const XT *win = reinterpret_cast<const XT *>(S.win(w));
+                    const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols<VT, XT>(w)) - (d.a & ~7);
+                    const XT *win = S.win<VT, XT>(w);
                     sum = row_sum<AT>(k0, k1, [&](int k) { return (int)lc[k]; },
                                       [&](int c2) { return AT(win[c2]); }, vs);
                 } else {
-                    const int32_t *cs = S.cols(w) - (d.a & ~3);
+                    const int32_t *cs = S.cols<VT, XT>(w) - (d.a & ~3);
                     sum = row_sum<AT>(k0, k1, [&](int k) { return cs[k]; },
                                       [&](int c2) { return AT(x[c2]); }, vs);
                 }
@@ -506,7 +509,7 @@ __device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe 
         // windows of tiles whose matrix part was issued during the last pass
         while (pp.win_issued < pp.issued) {
             const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
-            issue_window<XT>(P, S, d, w, x);
+            issue_window<VT, XT>(P, S, d, w, x);
             ++pp.win_issued;
         }
         issue_next<VT, XT>(P, S, pp, t0, m, limit, pass_end, vals, x);
@@ -532,7 +535,7 @@ __device__ __forceinline__ bool spmv_tiles(const Params &P, const Smem &S, Pipe 
 // targets shared memory after the CTA exits.  A prefetched tile whose window
 // was never issued cannot complete its phase, so the window is issued first
 // (from any vector: the data is not used).
-template <class XT>
+template <class VT, class XT>
 __device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp, const XT *any_x) {
     const int w = threadIdx.x >> 5;
     const int t0 = P.cta_tile[blockIdx.x], nt = P.cta_tile[blockIdx.x + 1] - t0;
@@ -540,7 +543,7 @@ __device__ __forceinline__ void drain(const Params &P, const Smem &S, Pipe &pp, 
     if (m > 0) {
         while (pp.win_issued < pp.issued) {
             const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(pp.win_issued % (uint32_t)m));
-            issue_window<XT>(P, S, d, w, any_x);
+            issue_window<VT, XT>(P, S, d, w, any_x);
             ++pp.win_issued;
         }
         if ((threadIdx.x & 31) == 0) {

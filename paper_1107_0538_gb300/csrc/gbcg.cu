@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
         atomicCAS(&P.st->status, 0, status);
     }
 out:
-    drain<double>(P, S, pipe, p);
+    drain<double, double>(P, S, pipe, p);
 }
 
 // ---------------------------------------------- mixed-precision solve
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
         atomicCAS(&P.st->status, 0, status);
     }
 out:
-    drain<float>(P, S, pipe, P.p32);
+    drain<float, float>(P, S, pipe, P.p32);
 }
 
 // ------------------------------------------------------- plain SpMV kernel
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
     Pipe pipe;
     EpiStore epi{P.q};
     (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, epi, true);
-    drain<double>(P, S, pipe, P.x);
+    drain<double, double>(P, S, pipe, P.x);
 }
 
 using SolveKernel = void (*)(Params);

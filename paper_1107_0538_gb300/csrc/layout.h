@@ -22,7 +22,7 @@ constexpr int kThreads = 512;                  // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kTileRows = 32;                  // rows per warp tile (one per lane)
 constexpr int kTileNnz = 864;                  // stored entries per warp tile (32 rows x 27)
-constexpr int kWinMax = 448;                   // elements of x-window per tile
+constexpr int kWinMax = 440;                   // elements of x-window per tile
 constexpr int kSegAlign = 4;                   // window segments start/end on 4 elements:
                                                // 16-byte TMA alignment for FP64 and FP32 vectors
 constexpr int kSegMax = 32;                    // window segments per tile (one per lane)
@@ -30,7 +30,21 @@ constexpr int kBatch = 9;                      // loads in flight per thread
 constexpr int kValsStage = kTileNnz + 8;       // doubles per stage (alignment slack)
 constexpr int kColsStage = kTileNnz + 8;       // int32 (or 2x uint16) per stage
 constexpr int kRptrStage = kTileRows + 8;      // int32 per stage (row pointers)
-constexpr int kStageBytes = kValsStage * 8 + kColsStage * 4 + kRptrStage * 4 + kWinMax * 8;
+constexpr int kStageBytes = 14208;             // holds every layout below
+
+// Offsets inside a stage for stored values of VB bytes and vector elements of
+// XB bytes: values, column indices (int32, or uint16 for windowed tiles), row
+// pointers, x-window.
+template <int VB, int XB>
+struct StageLayout {
+    static constexpr int vals_off = 0;
+    static constexpr int cols_off = ((kValsStage * VB + 15) / 16) * 16;
+    static constexpr int rptr_off = cols_off + kColsStage * 4;
+    static constexpr int win_off = rptr_off + kRptrStage * 4;
+    static constexpr int end = win_off + kWinMax * XB;
+    static_assert(end <= kStageBytes, "stage too small for this value/vector type");
+    static_assert(cols_off % 16 == 0 && rptr_off % 16 == 0 && win_off % 16 == 0, "stage alignment");
+};
 constexpr int kRedSlots = 4;                   // partial sums per CTA per barrier
 constexpr int kSmemBytes = kWarps * kStageBytes + kWarps * 8 /*mbarriers*/ +
                            kThreads * 8 /*block-sum transpose*/ + 64 /*broadcast*/ + 64 /*control*/;

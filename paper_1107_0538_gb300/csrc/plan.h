@@ -19,7 +19,7 @@ inline I4 mk4(int32_t x, int32_t y, int32_t z, int32_t w) { return I4{x, y, z, w
 
 // Row tiles: at most kTileRows rows and kTileNnz entries each; a row with
 // more than kTileNnz entries is a tile of its own (read from global memory).
-std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, int *max_nnz) {
+inline std::vector<int32_t> plan_tiles(int32_t n, const std::vector<int32_t> &rowptr, int *max_nnz) {
     std::vector<int32_t> tiles;
     tiles.reserve(n / 16 + 2);
     int32_t r = 0;
@@ -57,7 +57,7 @@ struct TilePlan {
     int windowed = 0;
 };
 
-TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
+inline TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
                       const std::vector<int32_t> &tiles) {
     TilePlan tp;
     const int nt = (int)tiles.size() - 1;
@@ -142,7 +142,7 @@ TilePlan plan_windows(int32_t n, const std::vector<int32_t> &rowptr, const std::
 }
 
 // Contiguous tile ranges per CTA with about equal cost (entries + rows).
-std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::vector<int32_t> &rowptr,
+inline std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::vector<int32_t> &rowptr,
                                  int ctas) {
     const int nt = (int)tiles.size() - 1;
     std::vector<double> prefix(nt + 1, 0.0);
@@ -164,6 +164,111 @@ std::vector<int32_t> split_tiles(const std::vector<int32_t> &tiles, const std::v
     return cut;
 }
 
+
+// Batch of independent systems laid out as one block-diagonal matrix: row
+// tiles never cross a system boundary, each tile knows its system, and every
+// (CTA, system) pair with tiles on that CTA is a reduction segment.  Segments
+// are ordered by CTA and by system at once, so each CTA owns a contiguous run
+// of segments and so does each system.
+struct BatchPlan {
+    std::vector<int32_t> tiles;        // row boundaries (ntiles + 1)
+    std::vector<int32_t> tile_sys;     // system of each tile
+    std::vector<int32_t> cut;          // CTA -> tile range (ctas + 1)
+    std::vector<int32_t> cta_sys0;     // first system of each CTA (ctas + 1; last = nsys)
+    std::vector<int32_t> cta_nsys;     // systems of each CTA
+    std::vector<int32_t> cta_seg0;     // first segment of each CTA (ctas + 1)
+    std::vector<int32_t> sys_seg0;     // first segment of each system (nsys + 1)
+    std::vector<int32_t> sys_cta0;     // first CTA holding each system
+    std::vector<int32_t> seg_cta;      // CTA of each segment
+    int max_nsys_per_cta = 0;
+};
+
+inline BatchPlan plan_batch(const std::vector<int32_t> &rowptr, const std::vector<int32_t> &sys_rows,
+                            int ctas, int *max_tile_nnz) {
+    BatchPlan bp;
+    const int nsys = (int)sys_rows.size() - 1;
+    *max_tile_nnz = 0;
+    for (int s = 0; s < nsys; ++s) {
+        const int r0 = sys_rows[s], r1 = sys_rows[s + 1];
+        int r = r0;
+        while (r < r1) {
+            const int start = r;
+            if (rowptr[r + 1] - rowptr[r] > kTileNnz) {
+                ++r;
+            } else {
+                while (r < r1 && r - start < kTileRows && rowptr[r + 1] - rowptr[r] <= kTileNnz &&
+                       rowptr[r + 1] - rowptr[start] <= kTileNnz)
+                    ++r;
+            }
+            bp.tiles.push_back(start);
+            bp.tile_sys.push_back(s);
+            *max_tile_nnz = std::max(*max_tile_nnz, rowptr[r] - rowptr[start]);
+        }
+    }
+    bp.tiles.push_back(sys_rows[nsys]);
+    const int nt = (int)bp.tile_sys.size();
+    bp.cut = split_tiles(bp.tiles, rowptr, ctas);
+    bp.cta_sys0.assign(ctas + 1, 0);
+    bp.cta_nsys.assign(ctas, 0);
+    bp.cta_seg0.assign(ctas + 1, 0);
+    bp.sys_seg0.assign(nsys + 1, 0);
+    bp.sys_cta0.assign(nsys, -1);
+    std::vector<int32_t> seg_sys;
+    for (int c = 0; c < ctas; ++c) {
+        bp.cta_seg0[c] = (int)seg_sys.size();
+        const int t0 = bp.cut[c], t1 = bp.cut[c + 1];
+        if (t1 <= t0) continue;
+        const int s0 = bp.tile_sys[t0], s1 = bp.tile_sys[t1 - 1];
+        bp.cta_sys0[c] = s0;
+        bp.cta_nsys[c] = s1 - s0 + 1;
+        for (int s = s0; s <= s1; ++s) {
+            if (bp.sys_cta0[s] < 0) bp.sys_cta0[s] = c;
+            bp.seg_cta.push_back(c);
+            seg_sys.push_back(s);
+        }
+        bp.max_nsys_per_cta = std::max(bp.max_nsys_per_cta, s1 - s0 + 1);
+    }
+    bp.cta_seg0[ctas] = (int)seg_sys.size();
+    bp.cta_sys0[ctas] = nsys;
+    // the segments of each system follow each other (seg_sys never decreases)
+    for (int s = 0; s <= nsys; ++s)
+        bp.sys_seg0[s] = (int)(std::lower_bound(seg_sys.begin(), seg_sys.end(), s) - seg_sys.begin());
+    (void)nt;
+    return bp;
+}
+
+// Checks the batch plan: tiles inside one system, CTA system ranges and
+// segments consistent in both orders.  Empty string when sound.
+inline std::string check_batch_plan(const BatchPlan &bp, const std::vector<int32_t> &sys_rows, int ctas) {
+    const int nsys = (int)sys_rows.size() - 1;
+    const int nt = (int)bp.tile_sys.size();
+    for (int t = 0; t < nt; ++t) {
+        const int s = bp.tile_sys[t];
+        if (s < 0 || s >= nsys || bp.tiles[t] < sys_rows[s] || bp.tiles[t + 1] > sys_rows[s + 1])
+            return "tile " + std::to_string(t) + " crosses a system";
+    }
+    int k = 0;
+    for (int c = 0; c < ctas; ++c) {
+        if (bp.cta_seg0[c] != k) return "cta segment start";
+        for (int j = 0; j < bp.cta_nsys[c]; ++j, ++k) {
+            const int s = bp.cta_sys0[c] + j;
+            if (k >= (int)bp.seg_cta.size() || bp.seg_cta[k] != c) return "segment cta";
+            if (k < bp.sys_seg0[s] || k >= bp.sys_seg0[s + 1]) return "segment outside its system run";
+        }
+        for (int t = bp.cut[c]; t < bp.cut[c + 1]; ++t) {
+            const int s = bp.tile_sys[t];
+            if (s < bp.cta_sys0[c] || s >= bp.cta_sys0[c] + bp.cta_nsys[c]) return "tile system outside cta range";
+        }
+    }
+    for (int s = 0; s < nsys; ++s) {
+        for (int q = bp.sys_seg0[s]; q < bp.sys_seg0[s + 1]; ++q) {
+            const int c = bp.seg_cta[q];
+            if (s < bp.cta_sys0[c] || s >= bp.cta_sys0[c] + bp.cta_nsys[c]) return "system segment on wrong cta";
+        }
+        if (sys_rows[s + 1] > sys_rows[s] && bp.sys_seg0[s + 1] <= bp.sys_seg0[s]) return "system without segments";
+    }
+    return std::string();
+}
 
 // Checks every address the kernels form from a plan: TMA source ranges inside
 // the (padded) arrays, copy sizes inside the stage regions, window segments

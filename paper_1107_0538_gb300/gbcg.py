@@ -28,7 +28,9 @@ CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
-           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_solve_noalloc")
+           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_solve_noalloc",
+           "cg_batch_create", "cg_batch_enqueue", "cg_batch_results", "cg_batch_solve",
+           "cg_batch_tune", "cg_batch_destroy")
 CG_NOALLOC_MAX_N = 262144
 
 
@@ -72,6 +74,16 @@ class cg_plan(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class cg_batch_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("relres", ctypes.c_double)]
+
+
+class cg_batch_tuning(ctypes.Structure):
+    _fields_ = [("inner_tol", ctypes.c_double), ("gather_tiles", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double)]
+
+
 _LIB = None
 _LOCK = threading.Lock()
 
@@ -108,6 +120,20 @@ def lib() -> ctypes.CDLL:
             L.cg_solve_noalloc.argtypes = [ctypes.POINTER(cg_csr), vp, vp, dbl, i32, vp,
                                            ctypes.POINTER(cg_info)]
             L.cg_solve_noalloc.restype = ctypes.c_int
+            L.cg_batch_create.argtypes = [ctypes.POINTER(cg_csr), i32, ctypes.POINTER(cg_opts), vp,
+                                          ctypes.POINTER(vp)]
+            L.cg_batch_create.restype = ctypes.c_int
+            L.cg_batch_enqueue.argtypes = [vp, vp, vp, i32, dbl, i32]
+            L.cg_batch_enqueue.restype = ctypes.c_int
+            L.cg_batch_results.argtypes = [vp, ctypes.POINTER(cg_batch_result)]
+            L.cg_batch_results.restype = ctypes.c_int
+            L.cg_batch_solve.argtypes = [vp, vp, vp, i32, dbl, i32, ctypes.POINTER(cg_batch_result),
+                                         ctypes.POINTER(dbl)]
+            L.cg_batch_solve.restype = ctypes.c_int
+            L.cg_batch_tune.argtypes = [vp, vp, vp, i32, dbl, ctypes.POINTER(cg_batch_tuning)]
+            L.cg_batch_tune.restype = ctypes.c_int
+            L.cg_batch_destroy.argtypes = [vp]
+            L.cg_batch_destroy.restype = None
             _LIB = L
     return _LIB
 
@@ -246,6 +272,109 @@ class Solver:
     def close(self) -> None:
         if getattr(self, "h", None):
             cg_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+def cg_batch_create(systems, opts: cg_opts | None, stream: int | None) -> tuple[int, int | None]:
+    """systems: a ctypes array of cg_csr.  Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    rc = lib().cg_batch_create(systems, len(systems), ctypes.byref(opts) if opts is not None else None,
+                               ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    return rc, (h.value if rc == CG_OK else None)
+
+
+def cg_batch_enqueue(h: int, b_ptr: int, x_ptr: int, nrhs: int, tol: float, maxit: int) -> int:
+    return lib().cg_batch_enqueue(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                                  int(nrhs), float(tol), int(maxit))
+
+
+def cg_batch_results(h: int, nsys: int, nrhs: int) -> tuple[int, list]:
+    res = (cg_batch_result * (nsys * nrhs))()
+    rc = lib().cg_batch_results(ctypes.c_void_p(h), res)
+    return rc, list(res)
+
+
+def cg_batch_solve(h: int, b_ptr: int, x_ptr: int, nsys: int, nrhs: int, tol: float,
+                   maxit: int) -> tuple[int, list, float]:
+    res = (cg_batch_result * (nsys * nrhs))()
+    ms = ctypes.c_double(0.0)
+    rc = lib().cg_batch_solve(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                              int(nrhs), float(tol), int(maxit), res, ctypes.byref(ms))
+    return rc, list(res), ms.value
+
+
+def cg_batch_tune(h: int, b_ptr: int, x_ptr: int, nrhs: int, tol: float) -> tuple[int, cg_batch_tuning]:
+    t = cg_batch_tuning()
+    rc = lib().cg_batch_tune(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(x_ptr),
+                             int(nrhs), float(tol), ctypes.byref(t))
+    return rc, t
+
+
+def cg_batch_destroy(h: int | None) -> None:
+    lib().cg_batch_destroy(ctypes.c_void_p(h or 0))
+
+
+class BatchSolver:
+    """Independent systems (CSR objects with numpy arrays) solved together on
+    the current CUDA device; right-hand sides and solutions are float64 torch
+    tensors of shape (nrhs, N), N the total row count (systems concatenated)."""
+
+    def __init__(self, systems, inner_values: int = CG_VALUES_FP32, precond: int = CG_PRECOND_NONE,
+                 inner_tol: float = 0.0, max_outer: int = 50, grid_ctas: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o = cg_opts_default()
+        o.inner_values = inner_values
+        o.precond = precond
+        o.inner_tol = inner_tol
+        o.max_outer = max_outer
+        o.grid_ctas = grid_ctas
+        arr = (cg_csr * len(systems))()
+        self._keep = []
+        for i, A in enumerate(systems):
+            c, keep = host_csr(A)
+            arr[i] = c
+            self._keep.append(keep)
+        rc, self.h = cg_batch_create(arr, o, self.stream.cuda_stream)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_batch_create")
+        self.nsys = len(systems)
+        self.sizes = [int(A.n) for A in systems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+
+    def solve(self, B, X, tol: float, maxit: int = 0):
+        assert B.shape == X.shape and B.shape[1] == self.n and B.is_contiguous() and X.is_contiguous()
+        rc, res, ms = cg_batch_solve(self.h, B.data_ptr(), X.data_ptr(), self.nsys, B.shape[0], tol, maxit)
+        return rc, res, ms
+
+    def enqueue(self, B, X, tol: float, maxit: int = 0) -> int:
+        return cg_batch_enqueue(self.h, B.data_ptr(), X.data_ptr(), B.shape[0], tol, maxit)
+
+    def results(self, nrhs: int):
+        return cg_batch_results(self.h, self.nsys, nrhs)
+
+    def tune(self, B, X, tol: float):
+        return cg_batch_tune(self.h, B.data_ptr(), X.data_ptr(), B.shape[0], tol)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            cg_batch_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -273,6 +273,55 @@ def cube_blobs(e: int = 50, blob_seed: int = 1, x_seed: int = 2, contrast: float
     return Problem(f"q1-{e}^3-blobs-c{contrast:g}", g, A, csr_times(A, xs), xs, tol, mass, nu)
 
 
+def source_currents(grid: Grid, mass: np.ndarray, seed: int, nsteps: int = 4, ncoils: int = 3) -> np.ndarray:
+    """Right-hand sides of time-stepped source currents, shape (nsteps, n).
+
+    Coil c is an axis-aligned box (corner U[0.1, 0.6]^3, size U[0.1, 0.4]^3 of
+    the box extent) with amplitude U[0.5, 2] and phase U[0, 2 pi), 8 draws of
+    the stream of `seed`; at step s the current density is
+    J = sum_c amp_c sin(2 pi s / nsteps + phase_c) 1[node in coil c] and the
+    right-hand side is b = M_L J (lumped mass).
+    """
+    u = uniform01(seed, 8 * ncoils).reshape(ncoils, 8)
+    x, y, z = grid.node_coords()
+    ext = np.array([grid.ex * grid.h, grid.ey * grid.h, grid.ez * grid.h])
+    out = np.zeros((nsteps, grid.n))
+    for c in range(ncoils):
+        lo = (0.1 + 0.5 * u[c, 0:3]) * ext
+        hi = lo + (0.1 + 0.3 * u[c, 3:6]) * ext
+        amp = 0.5 + 1.5 * u[c, 6]
+        phase = 2.0 * math.pi * u[c, 7]
+        inside = ((x >= lo[0]) & (x <= hi[0]) & (y >= lo[1]) & (y <= hi[1]) & (z >= lo[2]) & (z <= hi[2]))
+        inside = inside.reshape(-1).astype(np.float64)
+        for s in range(nsteps):
+            out[s] += amp * math.sin(2.0 * math.pi * s / nsteps + phase) * inside
+    return out * mass[None, :]
+
+
+def batch_systems(nsys: int, emin: int = 20, emax: int = 80, seed0: int = 1000, nrhs: int = 4):
+    """Independent systems of uneven Q1 boxes for batched solves.
+
+    System i uses seed s = seed0 + i: draws 0-2 of that stream give the
+    element counts Ex, Ey, Ez ~ U{emin..emax}, draw 3 the contrast
+    (log-uniform on [1e2, 1e4]; iron at nu = 1 / contrast); the iron blobs use
+    the stream of seed 10 s + 1 and the source currents (nrhs time steps) the
+    stream of seed 10 s + 2; h = 1 / max(Ex, Ey, Ez).  Returns a list of dicts
+    with A, B (nrhs x n), grid, mass and contrast.
+    """
+    out = []
+    for i in range(nsys):
+        s = seed0 + i
+        u = uniform01(s, 4)
+        ex, ey, ez = (emin + np.minimum((u[:3] * (emax - emin + 1)).astype(int), emax - emin)).tolist()
+        contrast = 10.0 ** (2.0 + 2.0 * u[3])
+        g = Grid(int(ex), int(ey), int(ez), 1.0 / max(ex, ey, ez))
+        nu = nu_blobs(g, seed=10 * s + 1, nu_iron=1.0 / contrast)
+        A, mass = q1_matrix(nu, g.h)
+        B = source_currents(g, mass, seed=10 * s + 2, nsteps=nrhs)
+        out.append({"A": A, "B": B, "grid": g, "mass": mass, "contrast": contrast})
+    return out
+
+
 def flops_per_iteration(n: int, nnz: int) -> int:
     """One SpMV (2 NNZ), two dot products (4 N) and three axpys (6 N): 2 NNZ + 10 N."""
     return 2 * nnz + 10 * n

@@ -61,6 +61,9 @@ int main(void) {
   F(cg_plan, n) F(cg_plan, nnz) F(cg_plan, ctas) F(cg_plan, threads) F(cg_plan, tiles)
   F(cg_plan, tile_nnz) F(cg_plan, stages) F(cg_plan, smem_bytes) F(cg_plan, lanes_per_row)
   F(cg_plan, l2_evict_first) F(cg_plan, reg_rows) F(cg_plan, window_tiles) F(cg_plan, device_bytes)
+  F(cg_batch_result, iters) F(cg_batch_result, outer) F(cg_batch_result, status) F(cg_batch_result, reserved)
+  F(cg_batch_result, relres)
+  F(cg_batch_tuning, inner_tol) F(cg_batch_tuning, gather_tiles) F(cg_batch_tuning, trials) F(cg_batch_tuning, best_ms)
   printf("\\"sizes\\": [%zu, %zu, %zu, %zu]}", sizeof(cg_csr), sizeof(cg_opts), sizeof(cg_info), sizeof(cg_plan));
   return 0;
 }
@@ -68,7 +71,7 @@ int main(void) {
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     c = json.loads(subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout)
-    for T in (gbcg.cg_csr, gbcg.cg_opts, gbcg.cg_info, gbcg.cg_plan):
+    for T in (gbcg.cg_csr, gbcg.cg_opts, gbcg.cg_info, gbcg.cg_plan, gbcg.cg_batch_result, gbcg.cg_batch_tuning):
         for name, ctype in T._fields_:
             off, size = c[f"{T.__name__}.{name}"]
             assert getattr(T, name).offset == off, (T.__name__, name)
@@ -173,3 +176,16 @@ def test_noalloc_rejects_sizes_beyond_its_workspace_without_gpu():
     c = gbcg.cg_csr(10, 0, 1, 1, 1, gbcg.CG_MEM_HOST)  # host arrays are not accepted
     rc, _ = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
     assert rc == gbcg.CG_EINVAL
+
+
+def test_batch_rejects_bad_arguments_without_gpu():
+    A = problems.cube_uniform(2).A
+    c, keep = gbcg.host_csr(A)
+    arr = (gbcg.cg_csr * 2)(c, c)
+    bad = gbcg.cg_opts_default()
+    bad.inner_values = 7
+    assert gbcg.cg_batch_create(arr, bad, None)[0] == gbcg.CG_EINVAL
+    broken = (gbcg.cg_csr * 1)(gbcg.cg_csr(A.n, A.nnz + 1, c.rowptr, c.colidx, c.vals, gbcg.CG_MEM_HOST))
+    assert gbcg.cg_batch_create(broken, None, None)[0] == gbcg.CG_EINVAL
+    assert gbcg.lib().cg_batch_create(None, 0, None, None, None) == gbcg.CG_EINVAL
+    gbcg.cg_batch_destroy(None)
