@@ -42,7 +42,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gbcg", "reference"], default="gbcg")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the 100^3 SpMV roofline, the Jacobi form and the CPU baseline")
+                    help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="only measure the full batched workload (256 systems, edges 20..80, 4 rhs)")
     return ap.parse_args()
 
 
@@ -186,6 +188,89 @@ def run_reference(args) -> None:
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sample: int) -> dict:
+    """Batched mixed-precision solves of nsys uneven Q1 boxes x 4 source-current
+    right-hand sides in one persistent launch; optional autotuning; CUDA graph
+    capture of the enqueue; error of sampled pairs against the FP64 oracle."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    t0 = time.perf_counter()
+    sl = problems.batch_systems(nsys, emin, emax, seed0=1000)
+    gen_s = time.perf_counter() - t0
+    n_tot = sum(s["A"].n for s in sl)
+    nnz_tot = sum(s["A"].nnz for s in sl)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    bs = gbcg.BatchSolver([s["A"] for s in sl], inner_values=gbcg.CG_VALUES_FP32,
+                          precond=gbcg.CG_PRECOND_JACOBI)
+    create_s = time.perf_counter() - t0
+    Bh = np.concatenate([s["B"] for s in sl], axis=1)
+    B = torch.from_numpy(Bh).to(dev).contiguous()
+    X = torch.zeros_like(B)
+    out = {"workload": f"{nsys} Q1 boxes, edges U{{{emin}..{emax}}}, contrast 1e2-1e4, 4 source-current rhs, "
+                       f"FP32 inner (Jacobi) + FP64 refinement to rel. residual {TOL:g}",
+           "systems": nsys, "rhs": 4, "n_total": n_tot, "nnz_total": nnz_tot,
+           "generate_s": round(gen_s, 2), "create_s": round(create_s, 2)}
+    if tune:
+        rc, ch = bs.tune(B, X, TOL)
+        out["tuned"] = {"status": rc, "inner_tol": ch.inner_tol, "gather_tiles": ch.gather_tiles,
+                        "trials": ch.trials, "best_ms": round(ch.best_ms, 3)}
+    rc, res, ms = bs.solve(B, X, TOL)  # warm-up
+    times = []
+    for _ in range(steps):
+        X.zero_()
+        torch.cuda.synchronize()
+        rc, res, ms = bs.solve(B, X, TOL)
+        times.append(ms)
+    ok = sum(1 for r in res if r.status == gbcg.CG_OK)
+    batch_ms = statistics.median(times)
+    out.update({"status": rc, "pairs_converged": ok, "pairs": len(res), "ms_per_batch": round(batch_ms, 3),
+                "ms_per_solve_amortised": round(batch_ms / len(res), 4),
+                "inner_iters_max": max(r.iters for r in res), "outer_max": max(r.outer for r in res),
+                "relres_max": max(r.relres for r in res)})
+    # graph capture of one enqueue
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            bsg = gbcg.BatchSolver([x["A"] for x in sl[:min(nsys, 8)]], inner_values=gbcg.CG_VALUES_FP32,
+                                   precond=gbcg.CG_PRECOND_JACOBI, stream=s)
+            n8 = bsg.n
+            Bg = B[:, :n8].contiguous()
+            Xg = torch.zeros_like(Bg)
+            bsg.enqueue(Bg, Xg, TOL)  # warm-up outside the capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                bsg.enqueue(Bg, Xg, TOL)
+        Xg.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        rcg, resg = bsg.results(4)
+        out["graph"] = {"captured": True, "replay_status": rcg,
+                        "pairs_converged": sum(1 for r in resg if r.status == gbcg.CG_OK)}
+        bsg.close()
+    except Exception as exc:  # report, do not hide
+        out["graph"] = {"captured": False, "error": str(exc)[:200]}
+    # error of sampled pairs against the FP64 oracle
+    import oracle
+    Xh = X.cpu().numpy()
+    errs = []
+    offs = np.concatenate([[0], np.cumsum([s["A"].n for s in sl])])
+    order = sorted(range(nsys), key=lambda i: sl[i]["A"].n)[:sample]
+    for i in order:
+        A = sl[i]["A"]
+        for r in range(4):
+            ref = oracle.cg(A, sl[i]["B"][r], tol=TOL, precond=1)["x"]
+            x = Xh[r, offs[i]:offs[i + 1]]
+            errs.append(float(np.linalg.norm(x - ref) / np.linalg.norm(ref)))
+    out["err_vs_fp64_oracle_max"] = max(errs) if errs else None
+    out["err_sample"] = f"{len(errs)} pairs of the {len(order)} smallest systems"
+    bs.close()
+    return out
 
 
 def run_gbcg(args) -> None:
@@ -359,6 +444,8 @@ def run_gbcg(args) -> None:
         }
         bs.close()
         line["gpu_launches"] += 0  # extras are outside the timed region
+        # --------------------------------------- batched solves (mini config)
+        line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
 
         # ----------------------------------------------- CPU oracle baseline
         if rank == 0 and world == 1:
@@ -378,6 +465,14 @@ def run_gbcg(args) -> None:
 
 def main():
     args = parse_args()
+    if args.batched_full:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1107_0538_gb300 import gbcg
+        gbcg.lib()
+        print(json.dumps({"batched_full": measure_batched(256, 20, 80, max(1, args.steps // 5), tune=False,
+                                                          sample=2)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
