@@ -322,6 +322,81 @@ def batch_systems(nsys: int, emin: int = 20, emax: int = 80, seed0: int = 1000, 
     return out
 
 
+def node_log_nu(grid: Grid, nu: np.ndarray) -> np.ndarray:
+    """log nu at the nodes: the mean of log nu over the (1 to 8) elements that
+    share each node, node order x fastest (float64, length n).  This is the
+    second input field of the learned preconditioner."""
+    ex, ey, ez = grid.ex, grid.ey, grid.ez
+    ln = np.log(np.asarray(nu, dtype=np.float64)).reshape(ez, ey, ex)
+    acc = np.zeros((ez + 1, ey + 1, ex + 1))
+    cnt = np.zeros_like(acc)
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                acc[dz:dz + ez, dy:dy + ey, dx:dx + ex] += ln
+                cnt[dz:dz + ez, dy:dy + ey, dx:dx + ex] += 1.0
+    return (acc / cnt).reshape(-1)
+
+
+LEARN_PARAMS = 7792  # W1 16x27, W2 16x16x27, Wg 16x27, bg 16
+
+
+def bf16_representable(v: np.ndarray) -> np.ndarray:
+    """Round float values to the nearest BF16 (ties to even), returned as float32."""
+    f = np.asarray(v, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def learn_init_params(seed: int = 7, noise: float = 0.01, gate_bias: float = 2.0) -> np.ndarray:
+    """Initial parameters of the learned preconditioner (float32, BF16-representable).
+
+    W1 and W2 start at the identity on the centre tap (channel 0 of W1, the
+    diagonal of W2) plus noise * N(0, 1) from the splitmix64 stream of ``seed``;
+    the gate convolution starts at zero and its bias at ``gate_bias``, so the
+    untrained preconditioner is sigmoid(gate_bias)^2 D^-1 plus small noise."""
+    ch, ntap, centre = 16, 27, 13
+    w1 = np.zeros((ch, ntap))
+    w1[0, centre] = 1.0
+    w2 = np.zeros((ch, ch, ntap))
+    for o in range(ch):
+        w2[o, o, centre] = 1.0
+    z = normal(seed, w1.size + w2.size)
+    w1 += noise * z[:w1.size].reshape(w1.shape)
+    w2 += noise * z[w1.size:].reshape(w2.shape)
+    wg = np.zeros((ch, ntap))
+    bg = np.full(ch, gate_bias)
+    theta = np.concatenate([w1.ravel(), w2.ravel(), wg.ravel(), bg])
+    assert theta.size == LEARN_PARAMS
+    return bf16_representable(theta)
+
+
+@dataclasses.dataclass
+class LearnInstance:
+    name: str
+    grid: Grid
+    A: CSR
+    b: np.ndarray
+    xstar: np.ndarray
+    lognu: np.ndarray
+
+
+def learn_instance(e: int, seed: int, contrast: float = 1e3) -> LearnInstance:
+    """A random-reluctivity instance for the learned preconditioner.
+
+    Q1 cube of e^3 elements (h = 1/e) with iron blobs from the stream of
+    ``seed`` at nu = 1/contrast, x* uniform[-1, 1] from the stream of
+    seed + 1 and b = A x*, so the true error of any iterate is known.
+    Training instances use seeds 10000 and up, test instances 20000 and up."""
+    g = Grid(e, e, e, 1.0 / e)
+    nu = nu_blobs(g, seed=seed, nu_iron=1.0 / contrast)
+    A, _ = q1_matrix(nu, g.h)
+    xs = 2.0 * uniform01(seed + 1, A.n) - 1.0
+    return LearnInstance(f"q1-{e}^3-blobs-c{contrast:g}-s{seed}", g, A, csr_times(A, xs), xs,
+                         node_log_nu(g, nu))
+
+
 def flops_per_iteration(n: int, nnz: int) -> int:
     """One SpMV (2 NNZ), two dot products (4 N) and three axpys (6 N): 2 NNZ + 10 N."""
     return 2 * nnz + 10 * n
