@@ -61,6 +61,9 @@ extern "C" {
 /* ---- preconditioners --------------------------------------------------- */
 #define CG_PRECOND_NONE 0    /* plain CG, as in Section IV                      */
 #define CG_PRECOND_JACOBI 1  /* z = diag(A)^-1 r (Jacobi-preconditioned CG)     */
+#define CG_PRECOND_LEARNED 2 /* learned convolutional preconditioner inside
+                                flexible CG, Jacobi-PCG as fallback (needs
+                                cg_set_learned before the first solve)         */
 
 /*
  * A square sparse matrix in CSR form (Section IV stores the FEM matrix this
@@ -122,6 +125,10 @@ typedef struct {
     double kernel_ms;        /* device time of the solve kernel (CUDA events)     */
     int32_t launches;        /* kernels this call launched                        */
     int32_t outer;           /* refinement steps applied (0 for plain CG)         */
+    int32_t reverted_at;     /* CG_PRECOND_LEARNED: iteration at which the solve
+                                switched to Jacobi-PCG (0 = before the first
+                                step), -1 if it never did; -1 otherwise          */
+    int32_t reserved;        /* 0                                                 */
 } cg_info;
 
 /* Read-only description of the launch plan of a handle. */
@@ -306,6 +313,116 @@ void cg_batch_destroy(cg_batch *h);
  */
 int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit,
                      void *stream, cg_info *info);
+
+/* ======================================================================
+ * Learned preconditioner and flexible CG.
+ *
+ * The paper (Section IV) runs CG without a preconditioner; these calls add
+ * one that it does not have.  For a Q1 matrix on the node grid of an
+ * Ex x Ey x Ez box (n = (Ex+1)(Ey+1)(Ez+1), nodes numbered x fastest) the
+ * preconditioner is
+ *     z = D^-1/2 L^T L D^-1/2 r,   L = C2 diag(g) C1,   D = diag(A),
+ * where C1 (1 -> 16 channels) and C2 (16 -> 16) are 3x3x3 correlations over
+ * the node grid with zeros outside it, L^T applies C2's and C1's adjoints
+ * (flipped taps, swapped channels) and g = sigmoid(Cg(log nu / 8) + bg) are
+ * 16 gate channels computed from the log-reluctivity field at the nodes.  It
+ * is linear in r, symmetric and positive semi-definite for any parameters.
+ * The residual is scaled by 1 / rms(D^-1/2 r) before the network (which the
+ * linearity cancels) so that BF16 sees values of order one.  Inference and
+ * training run on the tensor cores: BF16 weights and activations, FP32
+ * accumulation; the Krylov vectors stay FP64.
+ *
+ * Parameters: CG_LEARN_PARAMS floats, W1[o][t] (16 x 27), W2[o][c][t]
+ * (16 x 16 x 27), Wg[o][t] (16 x 27), bg[o] (16); tap t = 9 (dz+1) +
+ * 3 (dy+1) + (dx+1) reads the node at offset (dx, dy, dz).
+ * ==================================================================== */
+#define CG_LEARN_PARAMS 7792
+
+typedef struct cg_net cg_net;
+
+/* Network on the current device with the given parameters (host array of
+ * CG_LEARN_PARAMS floats; used in BF16 by the kernels, kept in FP32 for
+ * training).  CG_EINVAL for NULL arguments or non-finite parameters. */
+int cg_net_create(const float *params, cg_net **out);
+
+/* Copies the FP32 parameters to a host array of CG_LEARN_PARAMS floats. */
+int cg_net_get_params(const cg_net *net, float *params);
+
+/* Replaces the parameters (host array) and resets the optimizer state. */
+int cg_net_set_params(cg_net *net, const float *params);
+
+/* Frees the network (NULL is a no-op).  Handles that use it must not solve
+ * with CG_PRECOND_LEARNED afterwards. */
+void cg_net_destroy(cg_net *net);
+
+/*
+ * Attaches the learned preconditioner to a handle created with
+ * CG_PRECOND_LEARNED: the box has ex x ey x ez elements with
+ * (ex+1)(ey+1)(ez+1) == n, lognu holds log nu at each node (host, n floats,
+ * node order), net must stay alive while the handle solves with it (its
+ * current parameters are read at each solve).  stall_window (1..128, 0 =
+ * 50) and stall_factor (in (0, 1], 0 = 0.9) set the switch to Jacobi-PCG:
+ * when no residual norm of the last stall_window iterations is below
+ * stall_factor times the smallest one before them.  Allocates the
+ * activation buffers (about 200 bytes per node).  CG_EINVAL for a handle
+ * without CG_PRECOND_LEARNED, a grid that does not match n or whose padded
+ * x-extent exceeds 520 nodes, non-finite lognu or a net on another device.
+ *
+ * With a learned handle cg_solve runs flexible CG: alpha = rho / p.q,
+ * beta = -alpha (z_new . q) / rho, p = z_new + beta p, rho = r.z; a stall or
+ * r.z <= 0 restarts it as Jacobi-PCG from the current x for the rest of the
+ * solve (cg_info.reverted_at).  Statuses and stop test as for CG.
+ */
+int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez, const float *lognu,
+                   int32_t stall_window, double stall_factor);
+
+/* z = M r once with the attached network (device vectors of n doubles, on
+ * the handle's stream; synchronous).  r = 0 gives z = 0. */
+int cg_precond_apply(cg_handle *h, const double *r, double *z);
+
+/*
+ * Training pairs from restarted FP64 CG: starting from x = 0, for
+ * s = 0 .. count-1 it records r_s = b - A x and e_s = xstar - x (as floats,
+ * row s of the count x n device arrays r_out and e_out) and then runs
+ * `segment` plain CG iterations from x (each segment a fresh CG start).
+ * xstar must solve A xstar = b (e.g. b built as A xstar), so e_s is the
+ * true error of r_s.  Device pointers; synchronous.
+ */
+int cg_learn_pairs(cg_handle *h, const double *b, const double *xstar, int32_t segment, int32_t count,
+                   float *r_out, float *e_out);
+
+/* A set of training pairs over instances that share one grid. */
+typedef struct {
+    int32_t ninst;             /* instances                                         */
+    cg_handle *const *inst;    /* host array of ninst learned handles (cg_set_learned
+                                  done, same ex, ey, ez, same device as the net)  */
+    int64_t npairs;
+    const int32_t *pair_inst;  /* host, npairs: instance of each pair              */
+    const float *r;            /* device, npairs x n: residuals                     */
+    const float *e;            /* device, npairs x n: their true errors (A e = r)   */
+} cg_learn_set;
+
+/*
+ * Loss and gradient of the pairs listed in `pairs` (host, count indices into
+ * the set), without changing the network: the loss of a pair is
+ * (u - e_hat)^T A_hat (u - e_hat) / (2n) with A_hat = D^-1/2 A D^-1/2,
+ * s = D^-1/2 r, sigma = rms(s), u the network output for s / sigma before
+ * the final D^-1/2 scaling, e_hat = D^1/2 e / sigma; *loss receives the
+ * mean over the pairs and grad (host, CG_LEARN_PARAMS floats, may be NULL)
+ * its gradient.  Synchronous.
+ */
+int cg_learn_grad(cg_net *net, const cg_learn_set *set, const int64_t *pairs, int32_t count, double *loss,
+                  float *grad);
+
+/*
+ * Adam on the mean loss of mini-batches: step k uses the pairs
+ * order[k * batch .. k * batch + batch - 1] (host indices into the set),
+ * learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; the
+ * optimizer state persists in the net across calls.  losses (host, steps
+ * doubles, may be NULL) receives each step's mean loss.  Synchronous.
+ */
+int cg_learn_train(cg_net *net, const cg_learn_set *set, const int64_t *order, int32_t steps, int32_t batch,
+                   float lr, double *losses);
 
 #ifdef __cplusplus
 }

@@ -29,9 +29,10 @@
 #include <vector>
 
 #include "cg_device.cuh"
+#include "gbcg.h"
+#include "handle.h"
 #include "lowprec.h"
 #include "plan.h"
-#include "gbcg.h"
 
 using namespace gbcg;
 
@@ -584,7 +585,6 @@ __global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
     drain<double, double>(P, S, pipe, P.x);
 }
 
-using SolveKernel = void (*)(Params);
 constexpr int kRptChoices[] = {0, 1, 2, 4};
 SolveKernel solve_kernel_for(int rpt) {
     switch (rpt) {
@@ -599,54 +599,7 @@ SolveKernel solve_kernel_for(int rpt) {
 
 // =================================================================== host
 
-struct cg_handle {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cg_opts opts{};
-    int32_t n = 0;
-    int64_t nnz = 0;
-    int ctas = 0;
-    int ntiles = 0;
-    int rpt = 0;                      // rows per thread kept in registers (0: none)
-    SolveKernel kernel = nullptr;
-    int max_tile_nnz = 0;
-    int evict_first = 0;
-    int64_t device_bytes = 0;
-    // device arrays
-    int32_t *rowptr = nullptr, *colidx = nullptr, *cta_tile = nullptr, *cta_row = nullptr;
-    int4 *tiles = nullptr, *segs = nullptr;
-    uint16_t *lcol = nullptr;
-    int window_tiles = 0;
-    // mixed precision
-    float *vals32 = nullptr, *diag_lo = nullptr, *dinv32 = nullptr;
-    uint16_t *vals16 = nullptr;
-    float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
-    double *vals = nullptr, *dinv = nullptr;
-    double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
-    double *partials = nullptr, *b_dev = nullptr, *x_dev = nullptr;
-    unsigned int *bar = nullptr;
-    DevStatus *st = nullptr;
-    DevStatus *st_host = nullptr;  // pinned
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<void *> allocs;
-};
-
 namespace {
-
-int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? CG_ENOMEM : CG_ECUDA; }
-
-template <class T>
-int dev_alloc(cg_handle *h, T **p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    void *v = nullptr;
-    cudaError_t e = cudaMalloc(&v, count * sizeof(T));
-    if (e != cudaSuccess) return cuda_fail(e);
-    h->allocs.push_back(v);
-    h->device_bytes += (int64_t)(count * sizeof(T));
-    *p = static_cast<T *>(v);
-    return CG_OK;
-}
 
 void free_handle(cg_handle *h) {
     if (!h) return;
@@ -654,6 +607,7 @@ void free_handle(cg_handle *h) {
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
+    learn_free(h);
     for (void *p : h->allocs) cudaFree(p);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -662,18 +616,9 @@ void free_handle(cg_handle *h) {
     delete h;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
+}  // namespace
 
-Params base_params(const cg_handle *h) {
+Params gbcg::base_params(const cg_handle *h) {
     Params P{};
     P.n = h->n;
     P.rowptr = h->rowptr;
@@ -713,13 +658,17 @@ Params base_params(const cg_handle *h) {
     return P;
 }
 
+namespace {
+
 // Enqueues one solve on the handle's stream (no synchronization).
-int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit) {
+int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, int precond) {
     Params P = base_params(h);
     P.b = b;
     P.x = x;
     P.tol = tol;
     P.maxit = maxit;
+    P.precond = precond;
+    if (!precond) P.z = h->r;
     cudaError_t e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
@@ -752,6 +701,7 @@ int finish_solve(cg_handle *h, cg_info *info) {
     out.kernel_ms = ms;
     out.launches = 1;
     out.outer = s.outer;
+    out.reverted_at = -1;
     if (info) *info = out;
     return s.status;
 }
@@ -767,10 +717,24 @@ void empty_info(cg_info *info) {
     if (info) {
         *info = cg_info{};
         info->relres_true = 0.0;
+        info->reverted_at = -1;
     }
 }
 
 }  // namespace
+
+int gbcg::enqueue_fp64_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit,
+                             int precond) {
+    return enqueue_solve(h, b, x, tol, maxit, precond);
+}
+
+int gbcg::enqueue_spmv(cg_handle *h, const double *x, double *y) {
+    Params P = base_params(h);
+    P.x = const_cast<double *>(x);
+    P.q = y;
+    spmv_kernel<<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P);
+    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+}
 
 extern "C" {
 
@@ -816,7 +780,9 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     } else {
         cg_opts_default(&opts);
     }
-    if (opts.precond != CG_PRECOND_NONE && opts.precond != CG_PRECOND_JACOBI) return CG_EINVAL;
+    if (opts.precond != CG_PRECOND_NONE && opts.precond != CG_PRECOND_JACOBI && opts.precond != CG_PRECOND_LEARNED)
+        return CG_EINVAL;
+    if (opts.precond == CG_PRECOND_LEARNED && opts.inner_values != CG_VALUES_FP64) return CG_EINVAL;
     if (!(opts.wait_limit_s > 0.0) || !std::isfinite(opts.wait_limit_s) || opts.wait_limit_s > 3600.0)
         return CG_EINVAL;
     if (opts.grid_ctas < 0 || opts.debug_phantom_arrivals < 0 || opts.debug_phantom_arrivals > 1024)
@@ -863,7 +829,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         if (colidx[k] < 0 || colidx[k] >= n) return CG_EINVAL;
 
     std::vector<double> dinv;
-    if (opts.precond == CG_PRECOND_JACOBI) {
+    if (opts.precond != CG_PRECOND_NONE) {
         dinv.resize(n);
         for (int32_t i = 0; i < n; ++i) {
             double d = 0.0;
@@ -962,7 +928,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         (rc = dev_alloc(h, &h->bar, 64)) ||
         (rc = dev_alloc(h, &h->st, 1)))
         return fail(rc);
-    if (opts.precond == CG_PRECOND_JACOBI) {
+    if (opts.precond != CG_PRECOND_NONE) {
         if ((rc = dev_alloc(h, &h->z, (size_t)n)) || (rc = dev_alloc(h, &h->dinv, (size_t)n))) return fail(rc);
     } else {
         h->z = h->r;
@@ -1015,7 +981,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         e = cudaMemcpy(h->cta_tile, cut.data(), sizeof(int32_t) * cut.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(h->cta_row, cta_row.data(), sizeof(int32_t) * cta_row.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && opts.precond == CG_PRECOND_JACOBI && n > 0)
+    if (e == cudaSuccess && opts.precond != CG_PRECOND_NONE && n > 0)
         e = cudaMemcpy(h->dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && mixed && n > 0) {
         if (opts.inner_values == CG_VALUES_FP32) {
@@ -1050,13 +1016,14 @@ int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit
     }
     DeviceGuard g(h->device);
     if (maxit <= 0) maxit = h->n;
+    if (h->opts.precond == CG_PRECOND_LEARNED) return learn_solve(h, b, x, tol, maxit, info);
     // The solve works on the handle's padded, 16-byte aligned copy of x (the
     // TMA copies of x-windows need that alignment), copied in and out on the
     // stream.
     const size_t bytes = sizeof(double) * (size_t)h->n;
     if (cudaMemcpyAsync(h->x_dev, x, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         return CG_ECUDA;
-    if ((rc = enqueue_solve(h, b, h->x_dev, tol, maxit)) != CG_OK) return rc;
+    if ((rc = enqueue_solve(h, b, h->x_dev, tol, maxit, h->opts.precond)) != CG_OK) return rc;
     if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
         return CG_ECUDA;
     return finish_solve(h, info);
@@ -1075,7 +1042,14 @@ int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (cudaMemcpyAsync(h->b_dev, b, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->x_dev, x, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return CG_ECUDA;
-    if ((rc = enqueue_solve(h, h->b_dev, h->x_dev, tol, maxit)) != CG_OK) return rc;
+    if (h->opts.precond == CG_PRECOND_LEARNED) {
+        rc = learn_solve(h, h->b_dev, h->x_dev, tol, maxit, info);
+        if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return CG_ECUDA;
+        return rc;
+    }
+    if ((rc = enqueue_solve(h, h->b_dev, h->x_dev, tol, maxit, h->opts.precond)) != CG_OK) return rc;
     if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return CG_ECUDA;
     return finish_solve(h, info);

@@ -1,0 +1,1874 @@
+// Learned preconditioner for CG on Q1 node grids, flexible CG around it, and
+// the kernels that train it (sm_103a).
+//
+// The paper (Section IV) runs unpreconditioned CG; this file adds the
+// preconditioner z = D^-1/2 L^T L D^-1/2 r, L = C2 diag(g) C1, a
+// convolutional network over the node grid (C1: 1 -> 16 channels, C2:
+// 16 -> 16, 3x3x3 taps, gates g from log nu).  Everything the network touches
+// lives in a zero-padded node grid, channels last:
+//
+//   padded node (x+1, y+1, z+1), x fastest, (nx+2)(ny+2)(nz+2) positions plus
+//   a zero tail; a 16-channel BF16 activation is 32 bytes per position.
+//
+// A convolution is an implicit GEMM on the tensor cores (mma.sync m16n8k16,
+// BF16 in, FP32 accumulate): an M-tile is 16 consecutive positions of one
+// padded xy-plane, so each of the 27 taps reads 16 consecutive staged rows
+// (a constant shift of the tile); halo positions compute garbage that is
+// never stored, so every store goes to an interior node and the zero halo is
+// never overwritten.  A CTA (4 warps) takes kTL positions of kTZ planes; its
+// input (kTZ + 2 planes x kTL + 2 px + 2 positions) is staged once into
+// shared memory with a bank-conflict-free swizzle of the two 16-byte halves
+// of each row.
+//
+// Flexible CG runs as a CUDA graph of kUnroll iterations of seven kernels
+// (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, p update, SpMV + p.q,
+// x/r update + stop test); scalars are decided by the last CTA to finish each
+// reducing kernel (fixed-order sums: bitwise reproducible) and kept in a
+// device state block; kernels return at once after the solve is done.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "cg_device.cuh"
+#include "gbcg.h"
+#include "handle.h"
+#include "lowprec.h"
+
+using namespace gbcg;
+
+namespace {
+
+constexpr int kCh = 16, kTaps = 27, kTapsPad = 32, kCentre = 13;
+constexpr int kOffW1 = 0, kOffW2 = kCh * kTaps, kOffWg = kOffW2 + kCh * kCh * kTaps, kOffBg = kOffWg + kCh * kTaps;
+static_assert(kOffBg + kCh == CG_LEARN_PARAMS, "parameter layout");
+constexpr float kLogNuScale = 0.125f;
+
+constexpr int kTL = 64;          // padded xy positions per conv tile (4 M-tiles)
+constexpr int kTZ = 4;           // planes per conv tile (one warp each)
+constexpr int kCT = 128;         // threads of a conv CTA
+constexpr int kMTiles = kTL / 16;
+constexpr int kSlack = kTL + 64; // zero positions after the padded grid
+constexpr int kMaxPx = 522;      // staged rows must fit shared memory
+constexpr int kVT = 256;         // threads of the vector kernels
+constexpr int kMaxWindow = 128;
+constexpr int kUnroll = 6;       // iterations per graph launch
+
+constexpr int kModeLearned = 0, kModeJacobi = 1;
+
+// ----------------------------------------------------------------- geometry
+struct Geo {
+    int nx, ny, nz;       // nodes per axis
+    int px, py, pz;       // padded extents
+    int plane;            // px * py
+    int s_begin, s_len;   // interior xy range of a padded plane
+    int xy_chunks, z_chunks, tiles;
+    int rl;               // staged positions per plane: kTL + 2 px + 2
+    int n;                // nodes
+    long long npad;       // px py pz
+};
+
+Geo make_geo(int ex, int ey, int ez) {
+    Geo G{};
+    G.nx = ex + 1;
+    G.ny = ey + 1;
+    G.nz = ez + 1;
+    G.px = G.nx + 2;
+    G.py = G.ny + 2;
+    G.pz = G.nz + 2;
+    G.plane = G.px * G.py;
+    G.s_begin = G.px + 1;
+    G.s_len = (G.ny - 1) * G.px + G.nx;
+    G.xy_chunks = (G.s_len + kTL - 1) / kTL;
+    G.z_chunks = (G.nz + kTZ - 1) / kTZ;
+    G.tiles = G.xy_chunks * G.z_chunks;
+    G.rl = kTL + 2 * G.px + 2;
+    G.n = G.nx * G.ny * G.nz;
+    G.npad = (long long)G.px * G.py * G.pz;
+    return G;
+}
+
+size_t conv16_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTaps * kCh * kCh * 2; }
+size_t conv1_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 2 + 16; }
+size_t convout_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTaps * kCh * 2; }
+size_t wgrad16_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTZ * kTL * 32; }
+size_t wgrad1_smem(const Geo &G) {
+    return ((size_t)(kTZ + 2) * G.rl * 2 + 15) / 16 * 16 + 16 + (size_t)kTZ * kTL * 32 + 4 * 16 * 32 * 4;
+}
+
+// ---------------------------------------------------------------- device
+__device__ __forceinline__ int tap_dx(int t) { return t % 3 - 1; }
+__device__ __forceinline__ int tap_dy(int t) { return (t / 3) % 3 - 1; }
+__device__ __forceinline__ int tap_dz(int t) { return t / 9 - 1; }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+// D += A B, m16n8k16, A row-major 16x16 BF16, B column-major 16x8 BF16, FP32.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float2 unpack_bf16(uint32_t u) {
+    __nv_bfloat162 v = *reinterpret_cast<__nv_bfloat162 *>(&u);
+    return __bfloat1622float2(v);
+}
+__device__ __forceinline__ uint32_t pack_raw(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+
+// Row R (32 bytes: two 16-byte halves) of a swizzled staging buffer: half h
+// lives at (h ^ bit 2 of R), so 8 consecutive rows hit 8 distinct bank groups.
+__device__ __forceinline__ uint32_t row_addr(uint32_t base, int R, int h) {
+    return base + (uint32_t)R * 32u + ((uint32_t)(h ^ ((R >> 2) & 1)) << 4);
+}
+
+// Interior test of a padded position and its node index (-1 outside).
+__device__ __forceinline__ int node_of(const Geo &G, long long pos) {
+    const int z = (int)(pos / G.plane);
+    const int rem = (int)(pos - (long long)z * G.plane);
+    const int y = rem / G.px, x = rem - y * G.px;
+    if (x < 1 || x > G.nx || y < 1 || y > G.ny || z < 1 || z > G.nz) return -1;
+    return (x - 1) + G.nx * ((y - 1) + G.ny * (z - 1));
+}
+
+// Output position of row `row` (0..15) of M-tile m in warp w's plane;
+// returns the padded position, or -1 if it is not an interior node.
+__device__ __forceinline__ long long out_pos(const Geo &G, int s0, int z0, int w, int m, int row) {
+    const int zi = z0 + w;                 // interior plane index
+    const int s = s0 + 16 * m + row;       // padded xy index
+    if (zi >= G.nz || s >= G.s_begin + G.s_len) return -1;
+    const int x = s % G.px;
+    if (x < 1 || x > G.nx) return -1;
+    return (long long)(zi + 1) * G.plane + s;
+}
+
+// Stages the 16-channel input of a tile (kTZ + 2 planes x rl positions).
+__device__ __forceinline__ void stage16(const Geo &G, const __nv_bfloat16 *src, unsigned char *sm, int s0,
+                                        int z0) {
+    const int per_plane = G.rl * 2;
+    const int total = (kTZ + 2) * per_plane;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int lp = idx / per_plane, rem = idx - lp * per_plane;
+        const int j = rem >> 1, h = rem & 1;
+        const int R = lp * G.rl + j;
+        unsigned char *dst = sm + R * 32 + ((h ^ ((R >> 2) & 1)) << 4);
+        const int zin = z0 + lp;
+        if (zin < G.pz) {
+            const long long pos = (long long)zin * G.plane + (s0 - G.px - 1) + j;
+            cp_async16(dst, src + pos * kCh + h * 8);
+        } else {
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+// One-channel input of a tile, as BF16 (kTZ + 2 planes x rl positions):
+// from a padded BF16 field, or from a node-order vector v scaled by
+// dsq[i] * scale (the network input s_hat = D^-1/2 r / sigma).
+template <class VT>
+__device__ __forceinline__ void stage1(const Geo &G, const __nv_bfloat16 *src, const VT *v, const double *dsq,
+                                       double scale, uint16_t *sm, int s0, int z0) {
+    const int total = (kTZ + 2) * G.rl;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int lp = idx / G.rl, j = idx - lp * G.rl;
+        const int zin = z0 + lp;
+        uint16_t val = 0;
+        if (zin < G.pz) {
+            const long long pos = (long long)zin * G.plane + (s0 - G.px - 1) + j;
+            if (src) {
+                val = reinterpret_cast<const uint16_t *>(src)[pos];
+            } else {
+                const int i = node_of(G, pos);
+                if (i >= 0) {
+                    const float f = (float)((double)v[i] * dsq[i] * scale);
+                    __nv_bfloat16 b = __float2bfloat16_rn(f);
+                    val = *reinterpret_cast<uint16_t *>(&b);
+                }
+            }
+        }
+        sm[idx] = val;
+    }
+}
+
+// ------------------------------------------------------- solver state
+struct FcgState {
+    const double *b;
+    double *x;
+    double tol, bnorm, bb;
+    double rho, alpha, beta, rr, rdr, sigma, sigma_inv, zr, zq, pq, true_rr;
+    double best_before, factor;
+    double ring[kMaxWindow + 1];
+    int32_t n, iters, status, done, mode, restart, reverted_at, mode_start, maxit, window;
+    unsigned int counter;
+    int32_t pad;
+};
+
+// Flags the host polls after each graph launch (the same order as in FcgState).
+struct FcgFlags {
+    int32_t n, iters, status, done, mode;
+};
+
+struct ConvArgs {
+    Geo G;
+    const __nv_bfloat16 *in;     // padded input (16 channels, or 1 channel for conv1)
+    const double *res;           // conv1: node-order FP64 input (when in == nullptr)
+    const float *resf;           // conv1: node-order FP32 input (when in == nullptr and res == nullptr)
+    const double *dsq;           // 1 / sqrt(diag A)
+    const __nv_bfloat16 *w;      // packed weights of this convolution
+    const float *bias;           // E_SIGMOID
+    __nv_bfloat16 *out;          // padded 16-channel output
+    __nv_bfloat16 *pre;          // E_GATE_PRE: pre-gate output; E_BWD_GATE: pre-gate field read
+    const __nv_bfloat16 *gate;   // gates (padded, 16 channels)
+    float *dg;                   // E_BWD_GATE: gate-gradient field (padded, 16 channels, FP32)
+    int dg_add;                  // 0: dg = ..., 1: dg += ...
+    // conv_out
+    float *u;                    // E_OUT_U: node-order FP32 output
+    double *z;                   // E_OUT_Z / E_OUT_FCG
+    const double *r;             // E_OUT_FCG: residual (node order)
+    const double *q;             // E_OUT_FCG: A p of the last step
+    const double *dinv;          // Jacobi fallback
+    double *partials;
+    FcgState *st;                // solver state (nullptr: always run, scale from sigma_inv below)
+    const double *sigma;         // apply: {sigma, 1/sigma} for the input scale and the output
+};
+
+enum { E_STORE = 0, E_GATE = 1, E_GATE_PRE = 2, E_BWD_GATE = 3, E_SIGMOID = 4 };
+enum { E_OUT_U = 0, E_OUT_Z = 1, E_OUT_FCG = 2 };
+
+__device__ __forceinline__ bool conv_skip(const FcgState *st) {
+    return st && (st->done || st->mode != kModeLearned);
+}
+
+// 16-channel output of one warp's M-tiles: acc[m][nb][4] (rows g, g+8; columns 2t4, 2t4+1 of n-block nb).
+template <int EPI>
+__device__ __forceinline__ void store16(const ConvArgs &A, int s0, int z0, int w, float (&acc)[kMTiles][2][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int m = 0; m < kMTiles; ++m) {
+#pragma unroll
+        for (int hrow = 0; hrow < 2; ++hrow) {
+            const long long pos = out_pos(A.G, s0, z0, w, m, g + 8 * hrow);
+            if (pos < 0) continue;
+#pragma unroll
+            for (int nb = 0; nb < 2; ++nb) {
+                const int ch = nb * 8 + 2 * t4;
+                const long long e = pos * kCh + ch;
+                float v0 = acc[m][nb][2 * hrow], v1 = acc[m][nb][2 * hrow + 1];
+                if (EPI == E_SIGMOID) {
+                    v0 = 1.0f / (1.0f + __expf(-(v0 + A.bias[ch])));
+                    v1 = 1.0f / (1.0f + __expf(-(v1 + A.bias[ch + 1])));
+                    *reinterpret_cast<uint32_t *>(A.out + e) = pack_bf16(v0, v1);
+                } else if (EPI == E_STORE) {
+                    *reinterpret_cast<uint32_t *>(A.out + e) = pack_bf16(v0, v1);
+                } else {
+                    const float2 gv = unpack_bf16(*reinterpret_cast<const uint32_t *>(A.gate + e));
+                    if (EPI == E_GATE_PRE) *reinterpret_cast<uint32_t *>(A.pre + e) = pack_bf16(v0, v1);
+                    if (EPI == E_BWD_GATE) {
+                        const float2 pv = unpack_bf16(*reinterpret_cast<const uint32_t *>(A.pre + e));
+                        float2 *d = reinterpret_cast<float2 *>(A.dg + e);
+                        float2 dv = A.dg_add ? *d : make_float2(0.0f, 0.0f);
+                        dv.x = fmaf(pv.x, v0, dv.x);
+                        dv.y = fmaf(pv.y, v1, dv.y);
+                        *d = dv;
+                    }
+                    *reinterpret_cast<uint32_t *>(A.out + e) = pack_bf16(gv.x * v0, gv.y * v1);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- 16 -> 16 convolution
+// y[o, p] = sum_{t, c} K[t][o][c] x[c, p + off(t)], K packed [27][16][16].
+template <int EPI>
+__global__ void __launch_bounds__(kCT) conv16_kernel(ConvArgs A) {
+    if (conv_skip(A.st)) return;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Geo &G = A.G;
+    unsigned char *sw = sm + (size_t)(kTZ + 2) * G.rl * 32;
+    const int tile = blockIdx.x;
+    const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
+    const int z0 = (tile / G.xy_chunks) * kTZ;
+    stage16(G, A.in, sm, s0, z0);
+    // weights: row (t, o) of 32 bytes, swizzled like the input
+    for (int idx = threadIdx.x; idx < kTaps * kCh * 2; idx += blockDim.x) {
+        const int R = idx >> 1, h = idx & 1;
+        cp_async16(sw + R * 32 + ((h ^ ((R >> 2) & 1)) << 4), A.w + (size_t)R * kCh + h * 8);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t in_base = smem_u32(sm), w_base = smem_u32(sw);
+    float acc[kMTiles][2][4];
+#pragma unroll
+    for (int m = 0; m < kMTiles; ++m)
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[m][nb][k] = 0.0f;
+    const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
+    const int b_o = (lane & 7) + ((lane >> 4) << 3), b_half = (lane >> 3) & 1;
+#pragma unroll 3
+    for (int t = 0; t < kTaps; ++t) {
+        uint32_t b[4];
+        ldsm_x4(b, row_addr(w_base, t * kCh + b_o, b_half));
+        const int plane_row = (w + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px;
+#pragma unroll
+        for (int m = 0; m < kMTiles; ++m) {
+            uint32_t a[4];
+            ldsm_x4(a, row_addr(in_base, plane_row + 16 * m + a_row, a_half));
+            mma_bf16(acc[m][0], a, b[0], b[1]);
+            mma_bf16(acc[m][1], a, b[2], b[3]);
+        }
+    }
+    store16<EPI>(A, s0, z0, w, acc);
+}
+
+// --------------------------------------------------- 1 -> 16 convolution
+// y[o, p] = sum_t K[o][t] x[p + off(t)], K packed [16][32] (taps 27..31 zero):
+// the taps are the GEMM's K dimension, gathered from the staged plane.
+template <int EPI, class VT>
+__global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
+    if (conv_skip(A.st)) return;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Geo &G = A.G;
+    uint16_t *xs = reinterpret_cast<uint16_t *>(sm);
+    const int tile = blockIdx.x;
+    const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
+    const int z0 = (tile / G.xy_chunks) * kTZ;
+    double scale = 1.0;
+    if (!A.in) scale = A.st ? A.st->sigma_inv : A.sigma[1];
+    const VT *vin;
+    if constexpr (std::is_same<VT, double>::value) vin = A.res;
+    else vin = A.resf;
+    stage1<VT>(G, A.in, vin, A.dsq, scale, xs, s0, z0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+    // B fragments (whole K = 32 taps): b[ks][nb][2]
+    uint32_t b[2][2][2];
+    const uint32_t *wk = reinterpret_cast<const uint32_t *>(A.w);
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb) {
+            const int o = nb * 8 + g;
+            b[ks][nb][0] = wk[(o * kTapsPad + ks * 16 + 2 * t4) >> 1];
+            b[ks][nb][1] = wk[(o * kTapsPad + ks * 16 + 8 + 2 * t4) >> 1];
+        }
+    // staged offsets of the taps this lane gathers: k = ks*16 + {2t4, 2t4+1, 2t4+8, 2t4+9}
+    int off[2][4];
+    bool live[2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = ks * 16 + 2 * t4 + (u & 1) + (u >> 1) * 8;
+            live[ks][u] = t < kTaps;
+            const int tt = t < kTaps ? t : kCentre;
+            off[ks][u] = (1 + tap_dz(tt)) * G.rl + G.px + 1 + tap_dx(tt) + tap_dy(tt) * G.px;
+        }
+    float acc[kMTiles][2][4];
+#pragma unroll
+    for (int m = 0; m < kMTiles; ++m) {
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[m][nb][k] = 0.0f;
+        const int base = w * G.rl + 16 * m + g;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            uint16_t v[2][4];
+#pragma unroll
+            for (int hr = 0; hr < 2; ++hr)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[hr][u] = live[ks][u] ? xs[base + 8 * hr + off[ks][u]] : 0;
+            uint32_t a[4];
+            a[0] = pack_raw(v[0][0], v[0][1]);
+            a[1] = pack_raw(v[1][0], v[1][1]);
+            a[2] = pack_raw(v[0][2], v[0][3]);
+            a[3] = pack_raw(v[1][2], v[1][3]);
+            mma_bf16(acc[m][0], a, b[ks][0][0], b[ks][0][1]);
+            mma_bf16(acc[m][1], a, b[ks][1][0], b[ks][1][1]);
+        }
+    }
+    store16<EPI>(A, s0, z0, w, acc);
+}
+
+// ----------------------------------------------- deterministic reductions
+template <int NV>
+__device__ __forceinline__ void cta_sum(double (&v)[NV], double *sred) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        v[j] = warp_sum(v[j]);
+        if (lane == 0) sred[j * 32 + w] = v[j];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = warp_sum(lane < nw ? sred[j * 32 + lane] : 0.0);
+    }
+    __syncthreads();
+}
+
+// Publishes this CTA's partials (thread 0 holds them); true in every thread
+// of the last CTA to arrive, which then sums all partials in CTA order into
+// tot (thread 0) and resets the counter.
+template <int NV>
+__device__ __forceinline__ bool last_cta_totals(double (&v)[NV], double *partials, unsigned int *counter,
+                                                double (&tot)[NV], int *sflag) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) partials[(size_t)j * gridDim.x + blockIdx.x] = v[j];
+        __threadfence();
+        *sflag = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!*sflag) return false;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        const int G = (int)gridDim.x;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            double s = 0.0;
+            for (int m = lane; m < G; m += 32) s += __ldcg(partials + (size_t)j * G + m);
+            tot[j] = warp_sum(s);
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void finish(FcgState *st, int status) {
+    st->status = status;
+    st->done = 1;
+}
+
+// ------------------------------------------------ 16 -> 1 convolution
+// u[p] = sum_{t, c} K[t][c] x[c, p + off(t)] (K packed [27][16]); one real
+// output column of an n8 MMA.  EPI: E_OUT_U stores u (FP32, node order),
+// E_OUT_Z stores z = sigma D^-1/2 u, E_OUT_FCG also forms z.r and z.q and
+// takes the flexible-CG decisions (in the Jacobi fallback it forms
+// z = D^-1 r instead of running the network).
+template <int EPI>
+__global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
+    FcgState *st = A.st;
+    if (st && st->done) return;
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ double sred[2 * 32];
+    __shared__ int sflag;
+    const Geo &G = A.G;
+    const bool learned = !st || st->mode == kModeLearned;
+    double dzr = 0.0, dzq = 0.0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+    if (learned) {
+        unsigned char *sw = sm + (size_t)(kTZ + 2) * G.rl * 32;
+        const int tile = blockIdx.x;
+        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
+        const int z0 = (tile / G.xy_chunks) * kTZ;
+        stage16(G, A.in, sm, s0, z0);
+        for (int idx = threadIdx.x; idx < kTaps * 2; idx += blockDim.x)
+            cp_async16(sw + idx * 16, A.w + (size_t)idx * 8);
+        cp_async_wait_all();
+        __syncthreads();
+        const uint32_t in_base = smem_u32(sm);
+        const uint32_t *wk = reinterpret_cast<const uint32_t *>(sw);
+        float acc[kMTiles][4];
+#pragma unroll
+        for (int m = 0; m < kMTiles; ++m)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
+        const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
+#pragma unroll 3
+        for (int t = 0; t < kTaps; ++t) {
+            const uint32_t b0 = g == 0 ? wk[(t * kCh + 2 * t4) >> 1] : 0u;
+            const uint32_t b1 = g == 0 ? wk[(t * kCh + 8 + 2 * t4) >> 1] : 0u;
+            const int plane_row = (w + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px;
+#pragma unroll
+            for (int m = 0; m < kMTiles; ++m) {
+                uint32_t a[4];
+                ldsm_x4(a, row_addr(in_base, plane_row + 16 * m + a_row, a_half));
+                mma_bf16(acc[m], a, b0, b1);
+            }
+        }
+        if (t4 == 0) {
+            const double sigma = EPI == E_OUT_U ? 1.0 : (st ? st->sigma : A.sigma[0]);
+#pragma unroll
+            for (int m = 0; m < kMTiles; ++m)
+#pragma unroll
+                for (int hr = 0; hr < 2; ++hr) {
+                    const long long pos = out_pos(G, s0, z0, w, m, g + 8 * hr);
+                    if (pos < 0) continue;
+                    const int i = node_of(G, pos);
+                    const float u = acc[m][2 * hr];
+                    if (EPI == E_OUT_U) {
+                        A.u[i] = u;
+                    } else {
+                        const double zi = sigma * A.dsq[i] * (double)u;
+                        A.z[i] = zi;
+                        if (EPI == E_OUT_FCG) {
+                            dzr = fma(zi, A.r[i], dzr);
+                            dzq = fma(zi, A.q[i], dzq);
+                        }
+                    }
+                }
+        }
+    } else {
+        const int n = G.n;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const double zi = A.dinv[i] * A.r[i];
+            A.z[i] = zi;
+            dzr = fma(zi, A.r[i], dzr);
+            dzq = fma(zi, A.q[i], dzq);
+        }
+    }
+    if (EPI != E_OUT_FCG) return;
+    double v[2] = {dzr, dzq}, tot[2];
+    cta_sum<2>(v, sred);
+    if (!last_cta_totals<2>(v, A.partials, &st->counter, tot, &sflag)) return;
+    if (threadIdx.x == 0) {
+        const double zr = tot[0], zq = tot[1];
+        st->zr = zr;
+        st->zq = zq;
+        if (st->mode == kModeLearned && !(zr > 0.0)) {
+            // the network gave r.z <= 0 (or not finite): Jacobi-PCG from here on
+            st->mode = kModeJacobi;
+            st->reverted_at = st->iters;
+            st->mode_start = st->iters;
+            st->restart = 2;
+            st->rho = st->rdr;
+            st->beta = 0.0;
+        } else if (!finite_bits(zr)) {
+            finish(st, CG_ENAN);
+        } else if (!(zr > 0.0)) {
+            finish(st, CG_EBREAKDOWN);
+        } else {
+            st->beta = st->restart ? 0.0 : -st->alpha * zq / st->rho;
+            st->rho = zr;
+        }
+    }
+}
+
+// ------------------------------------------------------- vector kernels
+struct VecArgs {
+    int n;
+    FcgState *st;
+    double *x, *r, *z, *p, *q;
+    const double *dinv;
+    double *partials;
+};
+
+// p = z + beta p (p = z after a restart; p = D^-1 r after a switch to Jacobi).
+__global__ void __launch_bounds__(kVT) fcg_p_kernel(VecArgs V) {
+    const FcgState *st = V.st;
+    if (st->done) return;
+    const int restart = st->restart;
+    const double beta = st->beta;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x) {
+        if (restart == 2) V.p[i] = V.dinv[i] * V.r[i];
+        else if (restart == 1) V.p[i] = V.z[i];
+        else V.p[i] = fma(beta, V.p[i], V.z[i]);
+    }
+}
+
+// x += alpha p, r -= alpha q; r.r and r.D^-1 r; stop test, stall test.
+__global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
+    FcgState *st = V.st;
+    if (st->done) return;
+    __shared__ double sred[2 * 32];
+    __shared__ int sflag;
+    const double alpha = st->alpha;
+    double *x = st->x;
+    double rr = 0.0, rdr = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, V.p[i], x[i]);
+        const double ri = fma(-alpha, V.q[i], V.r[i]);
+        V.r[i] = ri;
+        rr = fma(ri, ri, rr);
+        rdr = fma(ri * V.dinv[i], ri, rdr);
+    }
+    double v[2] = {rr, rdr}, tot[2];
+    cta_sum<2>(v, sred);
+    if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag)) return;
+    // warp 0 of the last CTA: the residual-norm window for the stall test
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
+    const int k = st->iters + 1;
+    const double rn = sqrt(tot[0]);
+    const int W = st->window, RS = W + 1;
+    if (lane == 0) st->ring[k % RS] = rn;
+    __syncwarp();
+    double wmin = INFINITY;
+    for (int j = lane; j < W && j <= k; j += 32) wmin = fmin(wmin, st->ring[(k - j) % RS]);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) wmin = fmin(wmin, __shfl_xor_sync(0xffffffffu, wmin, m));
+    if (lane != 0) return;
+    st->iters = k;
+    st->rr = tot[0];
+    st->rdr = tot[1];
+    if (k >= W) st->best_before = fmin(st->best_before, st->ring[(k - W) % RS]);
+    if (!finite_bits(tot[0]) || !finite_bits(tot[1])) {
+        finish(st, CG_ENAN);
+        return;
+    }
+    if (rn <= st->tol * st->bnorm) {
+        finish(st, CG_OK);
+        return;
+    }
+    if (k >= st->maxit) {
+        finish(st, CG_ENOCONV);
+        return;
+    }
+    if (st->mode == kModeLearned && k - st->mode_start >= W && wmin > st->factor * st->best_before) {
+        st->mode = kModeJacobi;
+        st->reverted_at = k;
+        st->mode_start = k;
+        st->restart = 1;
+    }
+    st->sigma = sqrt(tot[1] / (double)V.n);
+    st->sigma_inv = st->sigma > 0.0 ? 1.0 / st->sigma : 0.0;
+}
+
+// ---------------------------------------------------------- SpMV kernels
+struct EpiSetupL {      // r = b - A x; r.r, b.b, r.D^-1 r
+    const double *b, *dinv;
+    double *r;
+    double rr = 0.0, bb = 0.0, rdr = 0.0;
+    __device__ __forceinline__ void row(int i, double ax, int) {
+        const double bi = b[i], ri = bi - ax;
+        r[i] = ri;
+        rr = fma(ri, ri, rr);
+        bb = fma(bi, bi, bb);
+        rdr = fma(ri * dinv[i], ri, rdr);
+    }
+};
+struct EpiQ {           // q = A p; p.q
+    const double *p;
+    double *q;
+    double pq = 0.0;
+    __device__ __forceinline__ void row(int i, double aq, int) {
+        q[i] = aq;
+        pq = fma(p[i], aq, pq);
+    }
+};
+struct EpiTrueL {       // ||b - A x||^2
+    const double *b;
+    double acc = 0.0;
+    __device__ __forceinline__ void row(int i, double ax, int) {
+        const double t = b[i] - ax;
+        acc = fma(t, t, acc);
+    }
+};
+
+struct EpiStoreY {      // y = A x
+    double *y;
+    __device__ __forceinline__ void row(int i, double ax, int) { y[i] = ax; }
+};
+
+enum { S_SETUP = 0, S_Q = 1, S_TRUE = 2 };
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgState *st, const double *vec,
+                                                                double *partials) {
+    if (MODE == S_Q && st->done) return;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    __shared__ int sflag;
+    init_pipeline(S);
+    Pipe pipe;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (MODE == S_SETUP) {
+        EpiSetupL e{st->b, P.dinv, P.r};
+        (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, vec, e, true);
+        v[0] = e.rr;
+        v[1] = e.bb;
+        v[2] = e.rdr;
+    } else if (MODE == S_Q) {
+        EpiQ e{vec, P.q};
+        (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, vec, e, true);
+        v[0] = e.pq;
+    } else {
+        EpiTrueL e{st->b};
+        (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, vec, e, true);
+        v[0] = e.acc;
+    }
+    drain<double, double>(P, S, pipe, vec);
+    block_sum<3>(v, S);
+    double tot[3];
+    if (!last_cta_totals<3>(v, partials, &st->counter, tot, &sflag)) return;
+    if (threadIdx.x != 0) return;
+    if (MODE == S_SETUP) {
+        st->rr = tot[0];
+        st->bb = tot[1];
+        st->rdr = tot[2];
+        st->bnorm = sqrt(tot[1]);
+        st->iters = 0;
+        st->mode = kModeLearned;
+        st->restart = 1;
+        st->reverted_at = -1;
+        st->mode_start = 0;
+        st->best_before = INFINITY;
+        st->ring[0] = sqrt(tot[0]);
+        st->sigma = sqrt(tot[2] / (double)P.n);
+        st->sigma_inv = st->sigma > 0.0 ? 1.0 / st->sigma : 0.0;
+        st->true_rr = -1.0;
+        if (!finite_bits(tot[0]) || !finite_bits(tot[1])) finish(st, CG_ENAN);
+        else if (tot[1] == 0.0) finish(st, CG_OK);
+        else if (sqrt(tot[0]) <= st->tol * st->bnorm) finish(st, CG_OK);
+    } else if (MODE == S_Q) {
+        const double pq = tot[0];
+        st->pq = pq;
+        st->restart = 0;
+        if (!finite_bits(pq)) finish(st, CG_ENAN);
+        else if (!(pq > 0.0)) finish(st, CG_EBREAKDOWN);
+        else st->alpha = st->rho / pq;
+    } else {
+        st->true_rr = tot[0];
+    }
+}
+
+// Plain y = A x for training (no reductions).
+__global__ void __launch_bounds__(kThreads, 1) spmv_store_kernel(Params P, const double *x, double *y) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    init_pipeline(S);
+    Pipe pipe;
+    EpiStoreY e{y};
+    (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, x, e, true);
+    drain<double, double>(P, S, pipe, x);
+}
+
+// ------------------------------------------------------------ training
+struct TrainArgs {
+    Geo G;
+    const float *r, *e;       // the pair (node order)
+    const double *dinv, *dsq;
+    double *scal;             // [0] sigma, [1] 1/sigma, [2] loss sum of the step, [3] counter space
+    unsigned int *counter;
+    double *partials;
+    __nv_bfloat16 *shat;      // padded, 1 channel
+    float *ehat;              // node order
+    const float *u;           // network output (node order)
+    float *v;                 // u - e_hat
+    double *t;                // D^-1/2 v (SpMV input)
+    const double *y;          // A t
+    __nv_bfloat16 *du;        // padded, 1 channel: A_hat v (n times the loss gradient)
+};
+
+__device__ __forceinline__ long long padded_of(const Geo &G, int i) {
+    const int x = i % G.nx, rest = i / G.nx;
+    const int y = rest % G.ny, z = rest / G.ny;
+    return (long long)(z + 1) * G.plane + (long long)(y + 1) * G.px + (x + 1);
+}
+
+// sigma = rms(D^-1/2 v) over a node-order vector (FP32 pair or FP64 residual).
+template <class VT>
+__global__ void __launch_bounds__(kVT) sigma_kernel(int n, const VT *v, const double *dinv, double *scal,
+                                                    unsigned int *counter, double *partials) {
+    __shared__ double sred[32];
+    __shared__ int sflag;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double vi = (double)v[i];
+        acc = fma(vi * dinv[i], vi, acc);
+    }
+    double a[1] = {acc}, tot[1];
+    cta_sum<1>(a, sred);
+    if (!last_cta_totals<1>(a, partials, counter, tot, &sflag)) return;
+    if (threadIdx.x == 0) {
+        const double sigma = sqrt(tot[0] / (double)n);
+        scal[0] = sigma;
+        scal[1] = sigma > 0.0 ? 1.0 / sigma : 0.0;
+    }
+}
+
+// s_hat (padded BF16) and e_hat = D^1/2 e / sigma (FP32, node order).
+__global__ void __launch_bounds__(kVT) pair_input_kernel(TrainArgs T) {
+    const double sinv = T.scal[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.G.n; i += gridDim.x * blockDim.x) {
+        const long long pos = padded_of(T.G, i);
+        T.shat[pos] = __float2bfloat16_rn((float)((double)T.r[i] * T.dsq[i] * sinv));
+        T.ehat[i] = (float)((double)T.e[i] / T.dsq[i] * sinv);
+    }
+}
+
+// v = u - e_hat, t = D^-1/2 v.
+__global__ void __launch_bounds__(kVT) loss_prep_kernel(TrainArgs T) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.G.n; i += gridDim.x * blockDim.x) {
+        const float vi = T.u[i] - T.ehat[i];
+        T.v[i] = vi;
+        T.t[i] = T.dsq[i] * (double)vi;
+    }
+}
+
+// w = D^-1/2 A t = A_hat v; loss += v.w / 2n; du = w (padded BF16).
+__global__ void __launch_bounds__(kVT) loss_kernel(TrainArgs T) {
+    __shared__ double sred[32];
+    __shared__ int sflag;
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.G.n; i += gridDim.x * blockDim.x) {
+        const double wi = T.dsq[i] * T.y[i];
+        acc = fma((double)T.v[i], wi, acc);
+        T.du[padded_of(T.G, i)] = __float2bfloat16_rn((float)wi);
+    }
+    double a[1] = {acc}, tot[1];
+    cta_sum<1>(a, sred);
+    if (!last_cta_totals<1>(a, T.partials, T.counter, tot, &sflag)) return;
+    if (threadIdx.x == 0) T.scal[2] += 0.5 * tot[0] / (double)T.G.n;
+}
+
+// dag = dg * g (1 - g) over the whole padded 16-channel field (zero halos stay zero).
+__global__ void __launch_bounds__(kVT) gate_grad_kernel(long long count, const float *dg, const __nv_bfloat16 *gate,
+                                                       __nv_bfloat16 *dag) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float gv = __bfloat162float(gate[k]);
+        dag[k] = __float2bfloat16_rn(dg[k] * gv * (1.0f - gv));
+    }
+}
+
+struct WgArgs {
+    Geo G;
+    const __nv_bfloat16 *dy;   // padded 16-channel field
+    const __nv_bfloat16 *x;    // padded field (16 channels for wgrad16, 1 for wgrad1)
+    float *part;               // gridDim.x x CG_LEARN_PARAMS partial gradients
+    int off;                   // parameter offset of this weight ([o][c][t] or [o][t])
+    int bias_off;              // wgrad1: offset of the channel sums of dy (-1: none)
+    int add;                   // 0: part = ..., 1: part += ...
+};
+
+// Stages the gradient tile dy (kTZ planes x kTL positions, no halo).
+__device__ __forceinline__ void stage_dy(const Geo &G, const __nv_bfloat16 *dy, unsigned char *sdy, int s0, int z0) {
+    for (int idx = threadIdx.x; idx < kTZ * kTL * 2; idx += blockDim.x) {
+        const int lp = idx / (kTL * 2), rem = idx - lp * (kTL * 2);
+        const int j = rem >> 1, h = rem & 1;
+        const int R = lp * kTL + j;
+        unsigned char *dst = sdy + R * 32 + ((h ^ ((R >> 2) & 1)) << 4);
+        const int zin = z0 + 1 + lp;
+        if (zin < G.pz) cp_async16(dst, dy + ((long long)zin * G.plane + s0 + j) * kCh + h * 8);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// G[o][c][t] = sum_p dy[o, p] x[c, p + off(t)] for 16-channel dy and x: a
+// GEMM over positions (M = o, N = c, K = p) per tap; warp w owns taps
+// w, w + 4, ...  Persistent over tiles; the CTA's sums go to part[blockIdx.x].
+__global__ void __launch_bounds__(kCT) wgrad16_kernel(WgArgs W) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Geo &G = W.G;
+    unsigned char *sdy = sm + (size_t)(kTZ + 2) * G.rl * 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+    constexpr int kMaxT = (kTaps + 3) / 4;
+    float acc[kMaxT][2][4];
+#pragma unroll
+    for (int i = 0; i < kMaxT; ++i)
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][nb][k] = 0.0f;
+    const uint32_t in_base = smem_u32(sm), dy_base = smem_u32(sdy);
+    const int a_pos = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+    const int b_pos = (lane & 7) + (((lane >> 3) & 1) << 3), b_half = lane >> 4;
+    for (int tile = blockIdx.x; tile < G.tiles; tile += gridDim.x) {
+        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
+        const int z0 = (tile / G.xy_chunks) * kTZ;
+        stage16(G, W.x, sm, s0, z0);
+        stage_dy(G, W.dy, sdy, s0, z0);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int ks = 0; ks < kTZ * kMTiles; ++ks) {
+            const int lp = ks / kMTiles, m = ks - lp * kMTiles;
+            uint32_t a[4];
+            ldsm_x4_t(a, row_addr(dy_base, lp * kTL + 16 * m + a_pos, a_half));
+#pragma unroll
+            for (int i = 0; i < kMaxT; ++i) {
+                const int t = w + 4 * i;
+                if (t < kTaps) {
+                    const int row = (lp + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px + 16 * m;
+                    uint32_t b[4];
+                    ldsm_x4_t(b, row_addr(in_base, row + b_pos, b_half));
+                    mma_bf16(acc[i][0], a, b[0], b[1]);
+                    mma_bf16(acc[i][1], a, b[2], b[3]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    float *part = W.part + (size_t)blockIdx.x * CG_LEARN_PARAMS + W.off;
+#pragma unroll
+    for (int i = 0; i < kMaxT; ++i) {
+        const int t = w + 4 * i;
+        if (t >= kTaps) continue;
+#pragma unroll
+        for (int nb = 0; nb < 2; ++nb)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int o = g + 8 * (k >> 1), c = nb * 8 + 2 * t4 + (k & 1);
+                float *dst = part + (o * kCh + c) * kTaps + t;
+                *dst = W.add ? *dst + acc[i][nb][k] : acc[i][nb][k];
+            }
+    }
+}
+
+// G[o][t] = sum_p dy[o, p] x[p + off(t)] for 16-channel dy and a 1-channel
+// x (taps are the GEMM's N dimension, 4 blocks of 8; "tap" 27 multiplies
+// by one and gives the channel sums of dy when bias_off >= 0).  Warps split
+// the positions and add their sums in shared memory at the end.
+__global__ void __launch_bounds__(kCT) wgrad1_kernel(WgArgs W) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Geo &G = W.G;
+    uint16_t *xs = reinterpret_cast<uint16_t *>(sm);
+    const size_t xs_bytes = ((size_t)(kTZ + 2) * G.rl * 2 + 15) / 16 * 16 + 16;
+    unsigned char *sdy = sm + xs_bytes;
+    float *sacc = reinterpret_cast<float *>(sdy + (size_t)kTZ * kTL * 32);   // [4 warps][16][32]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
+    float acc[4][4];
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[nb][k] = 0.0f;
+    const uint32_t dy_base = smem_u32(sdy);
+    const int a_pos = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
+    // staged offset of tap nb*8 + g (taps past 26: none)
+    int toff[4];
+    int tkind[4];   // 0 tap, 1 constant one, 2 zero
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb) {
+        const int t = nb * 8 + g;
+        tkind[nb] = t < kTaps ? 0 : (t == kTaps && W.bias_off >= 0 ? 1 : 2);
+        const int tt = t < kTaps ? t : kCentre;
+        toff[nb] = (1 + tap_dz(tt)) * G.rl + G.px + 1 + tap_dx(tt) + tap_dy(tt) * G.px;
+    }
+    for (int tile = blockIdx.x; tile < G.tiles; tile += gridDim.x) {
+        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
+        const int z0 = (tile / G.xy_chunks) * kTZ;
+        stage1<float>(G, W.x, nullptr, nullptr, 1.0, xs, s0, z0);
+        stage_dy(G, W.dy, sdy, s0, z0);
+        cp_async_wait_all();
+        __syncthreads();
+        for (int ks = w; ks < kTZ * kMTiles; ks += 4) {
+            const int lp = ks / kMTiles, m = ks - lp * kMTiles;
+            uint32_t a[4];
+            ldsm_x4_t(a, row_addr(dy_base, lp * kTL + 16 * m + a_pos, a_half));
+            const int base = lp * G.rl + 16 * m + 2 * t4;
+#pragma unroll
+            for (int nb = 0; nb < 4; ++nb) {
+                uint32_t b0, b1;
+                if (tkind[nb] == 0) {
+                    const uint16_t *xp = xs + base + toff[nb];
+                    b0 = pack_raw(xp[0], xp[1]);
+                    b1 = pack_raw(xp[8], xp[9]);
+                } else if (tkind[nb] == 1) {
+                    b0 = b1 = 0x3F803F80u;   // BF16 ones
+                } else {
+                    b0 = b1 = 0u;
+                }
+                mma_bf16(acc[nb], a, b0, b1);
+            }
+        }
+        __syncthreads();
+    }
+    // sum the four warps' accumulators: sacc[w][o][tap]
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int o = g + 8 * (k >> 1), tap = nb * 8 + 2 * t4 + (k & 1);
+            sacc[(w * 16 + o) * 32 + tap] = acc[nb][k];
+        }
+    __syncthreads();
+    float *part = W.part + (size_t)blockIdx.x * CG_LEARN_PARAMS;
+    for (int idx = threadIdx.x; idx < 16 * 32; idx += blockDim.x) {
+        const int o = idx >> 5, tap = idx & 31;
+        float s = 0.0f;
+#pragma unroll
+        for (int ww = 0; ww < 4; ++ww) s += sacc[(ww * 16 + o) * 32 + tap];
+        float *dst = nullptr;
+        if (tap < kTaps) dst = part + W.off + o * kTaps + tap;
+        else if (tap == kTaps && W.bias_off >= 0) dst = part + W.bias_off + o;
+        if (dst) *dst = W.add ? *dst + s : s;
+    }
+}
+
+// grad[j] += sum over CTAs (in order) of part[cta][j].
+__global__ void __launch_bounds__(kVT) grad_reduce_kernel(const float *part, int nparts, float *grad) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= CG_LEARN_PARAMS) return;
+    float s = 0.0f;
+    for (int c = 0; c < nparts; ++c) s += part[(size_t)c * CG_LEARN_PARAMS + j];
+    grad[j] += s;
+}
+
+struct NetDev {
+    float *theta, *m, *v, *grad;
+    __nv_bfloat16 *k1in, *k1t, *k2, *k2t, *kgin;
+    float *bg;
+    double *loss_hist;
+};
+
+// Packs parameter j into the kernels' BF16 layouts.
+__device__ __forceinline__ void pack_param(const NetDev &N, int j, float th) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(th);
+    if (j < kOffW2) {
+        const int o = j / kTaps, t = j % kTaps;
+        N.k1in[o * kTapsPad + t] = b;
+        N.k1t[(kTaps - 1 - t) * kCh + o] = b;
+    } else if (j < kOffWg) {
+        const int jj = j - kOffW2;
+        const int o = jj / (kCh * kTaps), c = (jj / kTaps) % kCh, t = jj % kTaps;
+        N.k2[(t * kCh + o) * kCh + c] = b;
+        N.k2t[((kTaps - 1 - t) * kCh + c) * kCh + o] = b;
+    } else if (j < kOffBg) {
+        const int jj = j - kOffWg;
+        N.kgin[(jj / kTaps) * kTapsPad + jj % kTaps] = b;
+    } else {
+        N.bg[j - kOffBg] = th;
+    }
+}
+
+// Adam step (lr > 0) on grad * scale, or (lr == 0) only the packing; clears
+// grad; records the step's mean loss.
+__global__ void __launch_bounds__(kVT) adam_kernel(NetDev N, float scale, float lr, float bc1, float bc2,
+                                                   double *scal, double loss_scale, int step_slot) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0 && step_slot >= 0) {
+        N.loss_hist[step_slot] = scal[2] * loss_scale;
+        scal[2] = 0.0;
+    }
+    if (j >= CG_LEARN_PARAMS) return;
+    float th = N.theta[j];
+    if (lr > 0.0f) {
+        const float gr = N.grad[j] * scale;
+        const float m = 0.9f * N.m[j] + 0.1f * gr;
+        const float v = 0.999f * N.v[j] + 0.001f * gr * gr;
+        N.m[j] = m;
+        N.v[j] = v;
+        th -= lr * (m / bc1) / (sqrtf(v / bc2) + 1e-8f);
+        N.theta[j] = th;
+    }
+    N.grad[j] = 0.0f;
+    pack_param(N, j, th);
+}
+
+// r_s = b - A x, e_s = xstar - x (as floats).
+__global__ void __launch_bounds__(kVT) pair_record_kernel(int n, const double *b, const double *xstar,
+                                                          const double *x, const double *ax, float *r, float *e) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        r[i] = (float)(b[i] - ax[i]);
+        e[i] = (float)(xstar[i] - x[i]);
+    }
+}
+
+__global__ void __launch_bounds__(kVT) dsq_kernel(int n, const double *dinv, double *dsq) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dsq[i] = sqrt(dinv[i]);
+}
+
+}  // namespace
+
+// ================================================================= host
+
+struct cg_net {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    NetDev d{};
+    void *block = nullptr;
+    long long step = 0;
+    // training workspace (allocated on first use, for one grid)
+    Geo tg{};
+    bool have_train = false;
+    std::vector<void *> tallocs;
+    __nv_bfloat16 *shat = nullptr, *a1 = nullptr, *h1 = nullptr, *h2 = nullptr, *kpre = nullptr, *k1 = nullptr;
+    __nv_bfloat16 *du = nullptr, *dk = nullptr, *dh2 = nullptr, *da1 = nullptr, *dag = nullptr;
+    float *dg = nullptr, *u = nullptr, *ehat = nullptr, *v = nullptr, *part = nullptr;
+    double *t = nullptr, *y = nullptr, *scal = nullptr, *partials = nullptr;
+    unsigned int *counter = nullptr;
+    int loss_cap_n = 0;
+    int wg_ctas = 0;
+    int vgrid = 0;
+};
+
+namespace gbcg {
+
+struct LearnCtx {
+    cg_net *net = nullptr;
+    Geo G{};
+    int window = 50;
+    double factor = 0.9;
+    std::vector<void *> allocs;
+    __nv_bfloat16 *lognu_in = nullptr, *gates = nullptr, *h1 = nullptr, *h2 = nullptr, *k1 = nullptr;
+    double *dsq = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    double *partials = nullptr, *sigma = nullptr;
+    unsigned int *counter = nullptr;
+    FcgState *st = nullptr;
+    DevStatus *dst = nullptr;
+    FcgState *st_host = nullptr;     // pinned
+    FcgFlags *flags_host = nullptr;  // pinned, 2 slots
+    DevStatus *dst_host = nullptr;   // pinned, 2 slots
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cg_net *graph_net = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    int vgrid = 0;
+};
+
+}  // namespace gbcg
+
+namespace {
+
+int sm_count(int dev) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+template <class T>
+int ctx_alloc(std::vector<void *> &allocs, T **p, size_t count, bool zero = true) {
+    *p = nullptr;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e);
+    allocs.push_back(v);
+    if (zero && cudaMemset(v, 0, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return CG_ECUDA;
+    *p = static_cast<T *>(v);
+    return CG_OK;
+}
+
+size_t act_count(const Geo &G, int ch) { return (size_t)(G.npad + kSlack) * ch; }
+
+// Lets every kernel use all the shared memory a block may opt in to, minus
+// its static shared memory (the two count against the same limit).
+int set_smem_limits() {
+    static int done = 0;
+    if (done) return CG_OK;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return CG_ECUDA;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f) {
+        cudaFuncAttributes fa{};
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - (int)fa.sharedSizeBytes);
+    };
+    set((const void *)conv16_kernel<E_STORE>);
+    set((const void *)conv16_kernel<E_GATE>);
+    set((const void *)conv16_kernel<E_GATE_PRE>);
+    set((const void *)conv16_kernel<E_BWD_GATE>);
+    set((const void *)convout_kernel<E_OUT_U>);
+    set((const void *)convout_kernel<E_OUT_Z>);
+    set((const void *)convout_kernel<E_OUT_FCG>);
+    set((const void *)wgrad16_kernel);
+    set((const void *)wgrad1_kernel);
+    set((const void *)fcg_spmv_kernel<S_SETUP>);
+    set((const void *)fcg_spmv_kernel<S_Q>);
+    set((const void *)fcg_spmv_kernel<S_TRUE>);
+    set((const void *)spmv_store_kernel);
+    if (e != cudaSuccess) return CG_ECUDA;
+    done = 1;
+    return CG_OK;
+}
+
+ConvArgs conv_args(const Geo &G) {
+    ConvArgs A{};
+    A.G = G;
+    return A;
+}
+
+// Gates g = sigmoid(Cg(lognu / 8) + bg) of an instance with the net's current parameters.
+void launch_gates(const LearnCtx *L, const cg_net *net, cudaStream_t s) {
+    ConvArgs A = conv_args(L->G);
+    A.in = L->lognu_in;
+    A.w = net->d.kgin;
+    A.bias = net->d.bg;
+    A.out = L->gates;
+    conv1_kernel<E_SIGMOID, double><<<L->G.tiles, kCT, conv1_smem(L->G), s>>>(A);
+}
+
+Params learn_params(cg_handle *h, LearnCtx *L) {
+    Params P = base_params(h);
+    P.r = L->r;
+    P.q = L->q;
+    P.z = L->z;
+    P.st = L->dst;
+    return P;
+}
+
+// One flexible-CG iteration: seven launches.
+void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
+    const Geo &G = L->G;
+    const cg_net *net = L->net;
+    ConvArgs A = conv_args(G);
+    A.st = L->st;
+    A.dsq = L->dsq;
+    A.gate = L->gates;
+    // h1 = g * C1(s_hat), s_hat = D^-1/2 r / sigma staged from r
+    A.in = nullptr;
+    A.res = L->r;
+    A.w = net->d.k1in;
+    A.out = L->h1;
+    conv1_kernel<E_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    // h2 = C2(h1)
+    A.in = L->h1;
+    A.res = nullptr;
+    A.w = net->d.k2;
+    A.out = L->h2;
+    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    // k1 = g * C2^T(h2)
+    A.in = L->h2;
+    A.w = net->d.k2t;
+    A.out = L->k1;
+    conv16_kernel<E_GATE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    // z = sigma D^-1/2 C1^T(k1) (or D^-1 r), z.r, z.q, beta
+    A.in = L->k1;
+    A.w = net->d.k1t;
+    A.z = L->z;
+    A.r = L->r;
+    A.q = L->q;
+    A.dinv = h->dinv;
+    A.partials = L->partials;
+    convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    VecArgs V{};
+    V.n = G.n;
+    V.st = L->st;
+    V.r = L->r;
+    V.z = L->z;
+    V.p = L->p;
+    V.q = L->q;
+    V.dinv = h->dinv;
+    V.partials = L->partials;
+    fcg_p_kernel<<<L->vgrid, kVT, 0, s>>>(V);
+    Params P = learn_params(h, L);
+    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, L->p, L->partials);
+    fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
+}
+
+int capture(cg_handle *h, LearnCtx *L) {
+    if (L->graph) {
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(L->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CG_ECUDA;
+    for (int u = 0; u < kUnroll; ++u) enqueue_body(h, L, L->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(L->cap_stream, &g);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&L->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        L->graph = nullptr;
+        cudaGetLastError();
+        return CG_ECUDA;
+    }
+    L->graph_net = L->net;
+    return CG_OK;
+}
+
+void free_ctx(LearnCtx *L) {
+    if (!L) return;
+    if (L->graph) cudaGraphExecDestroy(L->graph);
+    if (L->cap_stream) cudaStreamDestroy(L->cap_stream);
+    for (cudaEvent_t e : {L->ev[0], L->ev[1], L->t0, L->t1})
+        if (e) cudaEventDestroy(e);
+    for (void *p : L->allocs) cudaFree(p);
+    if (L->st_host) cudaFreeHost(L->st_host);
+    if (L->flags_host) cudaFreeHost(L->flags_host);
+    if (L->dst_host) cudaFreeHost(L->dst_host);
+    delete L;
+}
+
+bool finite_params(const float *p) {
+    for (int j = 0; j < CG_LEARN_PARAMS; ++j)
+        if (!std::isfinite(p[j])) return false;
+    return true;
+}
+
+int upload_params(cg_net *net, const float *params) {
+    if (cudaMemcpyAsync(net->d.theta, params, sizeof(float) * CG_LEARN_PARAMS, cudaMemcpyHostToDevice,
+                        net->stream) != cudaSuccess ||
+        cudaMemsetAsync(net->d.m, 0, sizeof(float) * CG_LEARN_PARAMS, net->stream) != cudaSuccess ||
+        cudaMemsetAsync(net->d.v, 0, sizeof(float) * CG_LEARN_PARAMS, net->stream) != cudaSuccess)
+        return CG_ECUDA;
+    net->step = 0;
+    adam_kernel<<<(CG_LEARN_PARAMS + kVT - 1) / kVT, kVT, 0, net->stream>>>(net->d, 0.0f, 0.0f, 1.0f, 1.0f, nullptr,
+                                                                             0.0, -1);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(net->stream) != cudaSuccess) return CG_ECUDA;
+    return CG_OK;
+}
+
+// Training workspace of the net for one grid.
+int ensure_train(cg_net *net, const Geo &G, int ninst_ctas) {
+    if (net->have_train && net->tg.nx == G.nx && net->tg.ny == G.ny && net->tg.nz == G.nz) return CG_OK;
+    for (void *p : net->tallocs) cudaFree(p);
+    net->tallocs.clear();
+    net->have_train = false;
+    net->tg = G;
+    net->wg_ctas = std::min(G.tiles, 2 * sm_count(net->device));
+    net->vgrid = std::min((G.n + kVT - 1) / kVT, 4 * sm_count(net->device));
+    const size_t a16 = act_count(G, kCh), a1 = act_count(G, 1);
+    auto &A = net->tallocs;
+    int rc;
+    if ((rc = ctx_alloc(A, &net->shat, a1)) || (rc = ctx_alloc(A, &net->a1, a16)) || (rc = ctx_alloc(A, &net->h1, a16)) ||
+        (rc = ctx_alloc(A, &net->h2, a16)) || (rc = ctx_alloc(A, &net->kpre, a16)) ||
+        (rc = ctx_alloc(A, &net->k1, a16)) || (rc = ctx_alloc(A, &net->du, a1)) || (rc = ctx_alloc(A, &net->dk, a16)) ||
+        (rc = ctx_alloc(A, &net->dh2, a16)) || (rc = ctx_alloc(A, &net->da1, a16)) ||
+        (rc = ctx_alloc(A, &net->dag, a16)) || (rc = ctx_alloc(A, &net->dg, a16)) ||
+        (rc = ctx_alloc(A, &net->u, (size_t)G.n)) || (rc = ctx_alloc(A, &net->ehat, (size_t)G.n)) ||
+        (rc = ctx_alloc(A, &net->v, (size_t)G.n)) || (rc = ctx_alloc(A, &net->t, (size_t)G.n + 16)) ||
+        (rc = ctx_alloc(A, &net->y, (size_t)G.n)) || (rc = ctx_alloc(A, &net->scal, 8)) ||
+        (rc = ctx_alloc(A, &net->counter, 4)) ||
+        (rc = ctx_alloc(A, &net->partials, (size_t)4 * std::max({net->vgrid, ninst_ctas, 1}))) ||
+        (rc = ctx_alloc(A, &net->part, (size_t)net->wg_ctas * CG_LEARN_PARAMS)))
+        return rc;
+    net->have_train = true;
+    return CG_OK;
+}
+
+// Loss and gradient of one pair, added to net->d.grad and scal[2] (stream net->stream).
+void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
+    LearnCtx *L = h->learn;
+    const Geo &G = L->G;
+    cudaStream_t s = net->stream;
+    TrainArgs T{};
+    T.G = G;
+    T.r = r;
+    T.e = e;
+    T.dinv = h->dinv;
+    T.dsq = L->dsq;
+    T.scal = net->scal;
+    T.counter = net->counter;
+    T.partials = net->partials;
+    T.shat = net->shat;
+    T.ehat = net->ehat;
+    T.u = net->u;
+    T.v = net->v;
+    T.t = net->t;
+    T.y = net->y;
+    T.du = net->du;
+    const int vg = net->vgrid;
+    sigma_kernel<float><<<vg, kVT, 0, s>>>(G.n, r, h->dinv, net->scal, net->counter, net->partials);
+    pair_input_kernel<<<vg, kVT, 0, s>>>(T);
+    launch_gates(L, net, s);
+    ConvArgs A = conv_args(G);
+    A.gate = L->gates;
+    // forward, keeping the pre-gate fields
+    A.in = net->shat;
+    A.w = net->d.k1in;
+    A.out = net->h1;
+    A.pre = net->a1;
+    conv1_kernel<E_GATE_PRE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    A.in = net->h1;
+    A.w = net->d.k2;
+    A.out = net->h2;
+    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.in = net->h2;
+    A.w = net->d.k2t;
+    A.out = net->k1;
+    A.pre = net->kpre;
+    conv16_kernel<E_GATE_PRE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.in = net->k1;
+    A.w = net->d.k1t;
+    A.u = net->u;
+    convout_kernel<E_OUT_U><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    // loss: v = u - e_hat, w = A_hat v
+    loss_prep_kernel<<<vg, kVT, 0, s>>>(T);
+    Params P = base_params(h);
+    P.st = L->dst;
+    spmv_store_kernel<<<h->ctas, kThreads, kSmemBytes, s>>>(P, net->t, net->y);
+    loss_kernel<<<vg, kVT, 0, s>>>(T);
+    // backward
+    WgArgs W{};
+    W.G = G;
+    W.part = net->part;
+    W.bias_off = -1;
+    // u = C1^T(k1): dk1 = C1(du); dk = g dk1, dg = k dk1; dW1 += wgrad(k1, du)
+    A.in = net->du;
+    A.w = net->d.k1in;
+    A.out = net->dk;
+    A.pre = net->kpre;
+    A.dg = net->dg;
+    A.dg_add = 0;
+    conv1_kernel<E_BWD_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    W.dy = net->k1;
+    W.x = net->du;
+    W.off = kOffW1;
+    W.add = 0;
+    wgrad1_kernel<<<net->wg_ctas, kCT, wgrad1_smem(G), s>>>(W);
+    // k = C2^T(h2): dh2 = C2(dk); dW2 += wgrad(h2, dk)
+    A.in = net->dk;
+    A.w = net->d.k2;
+    A.out = net->dh2;
+    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    W.dy = net->h2;
+    W.x = net->dk;
+    W.off = kOffW2;
+    W.add = 0;
+    wgrad16_kernel<<<net->wg_ctas, kCT, wgrad16_smem(G), s>>>(W);
+    // h2 = C2(h1): dW2 += wgrad(dh2, h1); dh1 = C2^T(dh2); da1 = g dh1, dg += a1 dh1
+    W.dy = net->dh2;
+    W.x = net->h1;
+    W.add = 1;
+    wgrad16_kernel<<<net->wg_ctas, kCT, wgrad16_smem(G), s>>>(W);
+    A.in = net->dh2;
+    A.w = net->d.k2t;
+    A.out = net->da1;
+    A.pre = net->a1;
+    A.dg_add = 1;
+    conv16_kernel<E_BWD_GATE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    // a1 = C1(s_hat): dW1 += wgrad(da1, s_hat)
+    W.dy = net->da1;
+    W.x = net->shat;
+    W.off = kOffW1;
+    W.add = 1;
+    wgrad1_kernel<<<net->wg_ctas, kCT, wgrad1_smem(G), s>>>(W);
+    // gates: dag = dg g (1 - g); dWg = wgrad(dag, lognu / 8), dbg = sum dag
+    const long long cnt = (long long)act_count(G, kCh);
+    gate_grad_kernel<<<4 * sm_count(net->device), kVT, 0, s>>>(cnt, net->dg, L->gates, net->dag);
+    W.dy = net->dag;
+    W.x = L->lognu_in;
+    W.off = kOffWg;
+    W.bias_off = kOffBg;
+    W.add = 0;
+    wgrad1_kernel<<<net->wg_ctas, kCT, wgrad1_smem(G), s>>>(W);
+    grad_reduce_kernel<<<(CG_LEARN_PARAMS + kVT - 1) / kVT, kVT, 0, s>>>(net->part, net->wg_ctas, net->d.grad);
+}
+
+int check_set(const cg_net *net, const cg_learn_set *set) {
+    if (!net || !set || set->ninst < 1 || !set->inst || set->npairs < 1 || !set->pair_inst || !set->r || !set->e)
+        return CG_EINVAL;
+    const cg_handle *h0 = set->inst[0];
+    if (!h0 || !h0->learn) return CG_EINVAL;
+    for (int i = 0; i < set->ninst; ++i) {
+        const cg_handle *h = set->inst[i];
+        if (!h || !h->learn || h->device != net->device) return CG_EINVAL;
+        const Geo &G = h->learn->G, &G0 = h0->learn->G;
+        if (G.nx != G0.nx || G.ny != G0.ny || G.nz != G0.nz) return CG_EINVAL;
+    }
+    for (int64_t k = 0; k < set->npairs; ++k)
+        if (set->pair_inst[k] < 0 || set->pair_inst[k] >= set->ninst) return CG_EINVAL;
+    return CG_OK;
+}
+
+int max_ctas(const cg_learn_set *set) {
+    int m = 1;
+    for (int i = 0; i < set->ninst; ++i) m = std::max(m, set->inst[i]->ctas);
+    return m;
+}
+
+}  // namespace
+
+void gbcg::learn_free(cg_handle *h) {
+    if (h && h->learn) {
+        free_ctx(h->learn);
+        h->learn = nullptr;
+    }
+}
+
+int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    LearnCtx *L = h->learn;
+    if (!L || !L->net) return CG_EINVAL;
+    cg_net *net = L->net;
+    const Geo &G = L->G;
+    cudaStream_t s = h->stream;
+    const size_t bytes = sizeof(double) * (size_t)h->n;
+    int rc = set_smem_limits();
+    if (rc != CG_OK) return rc;
+    if (L->graph_net != net || !L->graph) {
+        if ((rc = capture(h, L)) != CG_OK) return rc;
+    }
+    // the network's parameters may change between solves (training): make the
+    // net's stream's work visible first
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess) return CG_ECUDA;
+    FcgState init{};
+    init.b = b;
+    init.x = h->x_dev;
+    init.tol = tol;
+    init.n = h->n;
+    init.maxit = maxit;
+    init.window = L->window;
+    init.factor = L->factor;
+    init.reverted_at = -1;
+    *L->st_host = init;
+    cudaError_t e = cudaMemcpyAsync(h->x_dev, x, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->st, L->st_host, sizeof(FcgState), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->dst, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = cudaEventRecord(L->t0, s);
+    if (e != cudaSuccess) return CG_ECUDA;
+    int launches = 0;
+    launch_gates(L, net, s);
+    Params P = learn_params(h, L);
+    fcg_spmv_kernel<S_SETUP><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials);
+    launches += 2;
+    if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
+    // graph launches, two in flight; each body advances the iteration count
+    // by one until the solve is done, so maxit / kUnroll + 2 launches suffice
+    const int max_launch = maxit / kUnroll + 2;
+    int launched = 0, waited = 0;
+    bool stop = false;
+    while (!stop) {
+        while (launched - waited < 2 && launched < max_launch) {
+            const int sl = launched & 1;
+            e = cudaGraphLaunch(L->graph, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&L->flags_host[sl], &L->st->n, sizeof(FcgFlags), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&L->dst_host[sl], L->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(L->ev[sl], s);
+            if (e != cudaSuccess) return CG_ECUDA;
+            ++launched;
+            launches += 7 * kUnroll;
+        }
+        if (waited == launched) break;
+        const int sl = waited & 1;
+        if (cudaEventSynchronize(L->ev[sl]) != cudaSuccess) return CG_ECUDA;
+        ++waited;
+        const FcgFlags f = L->flags_host[sl];
+        if (f.done || L->dst_host[sl].status != 0) stop = true;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
+    if (h->opts.true_residual) {
+        fcg_spmv_kernel<S_TRUE><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials);
+        ++launches;
+    }
+    e = cudaEventRecord(L->t1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->st_host, L->st, sizeof(FcgState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->dst_host, L->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return CG_ECUDA;
+    const FcgState &st = *L->st_host;
+    int status = L->dst_host[0].status != 0 ? L->dst_host[0].status : (st.done ? st.status : CG_ENOCONV);
+    if (st.bb == 0.0 && status == CG_OK) {
+        if (cudaMemsetAsync(h->x_dev, 0, bytes, s) != cudaSuccess) return CG_ECUDA;
+    }
+    if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CG_ECUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, L->t0, L->t1);
+    if (info) {
+        cg_info out{};
+        out.iters = st.iters;
+        out.status = status;
+        out.relres = st.bnorm > 0.0 ? std::sqrt(st.rr) / st.bnorm : 0.0;
+        out.relres_true = (!h->opts.true_residual || status == CG_ENAN) ? -1.0
+                          : (st.bnorm > 0.0 ? std::sqrt(std::max(st.true_rr, 0.0)) / st.bnorm : 0.0);
+        out.kernel_ms = ms;
+        out.launches = launches;
+        out.outer = 0;
+        out.reverted_at = st.reverted_at;
+        *info = out;
+    }
+    return status;
+}
+
+extern "C" {
+
+int cg_net_create(const float *params, cg_net **out) {
+    if (!out) return CG_EINVAL;
+    *out = nullptr;
+    if (!params || !finite_params(params)) return CG_EINVAL;
+    cg_net *net = new (std::nothrow) cg_net();
+    if (!net) return CG_ENOMEM;
+    if (cudaGetDevice(&net->device) != cudaSuccess) {
+        delete net;
+        return CG_ECUDA;
+    }
+    auto fail = [&](int rc) {
+        cg_net_destroy(net);
+        return rc;
+    };
+    if (cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(CG_ECUDA);
+    const size_t P = CG_LEARN_PARAMS;
+    const size_t sizes[] = {P * 4, P * 4, P * 4, P * 4, kCh * kTapsPad * 2, kTaps * kCh * 2, kTaps * kCh * kCh * 2,
+                            kTaps * kCh * kCh * 2, kCh * kTapsPad * 2, kCh * 4, 8 * 4096};
+    size_t offs[11], total = 0;
+    for (int i = 0; i < 11; ++i) {
+        offs[i] = total;
+        total += (sizes[i] + 255) / 256 * 256;
+    }
+    if (cudaMalloc(&net->block, total) != cudaSuccess) return fail(CG_ENOMEM);
+    if (cudaMemset(net->block, 0, total) != cudaSuccess) return fail(CG_ECUDA);
+    char *b = static_cast<char *>(net->block);
+    net->d.theta = reinterpret_cast<float *>(b + offs[0]);
+    net->d.m = reinterpret_cast<float *>(b + offs[1]);
+    net->d.v = reinterpret_cast<float *>(b + offs[2]);
+    net->d.grad = reinterpret_cast<float *>(b + offs[3]);
+    net->d.k1in = reinterpret_cast<__nv_bfloat16 *>(b + offs[4]);
+    net->d.k1t = reinterpret_cast<__nv_bfloat16 *>(b + offs[5]);
+    net->d.k2 = reinterpret_cast<__nv_bfloat16 *>(b + offs[6]);
+    net->d.k2t = reinterpret_cast<__nv_bfloat16 *>(b + offs[7]);
+    net->d.kgin = reinterpret_cast<__nv_bfloat16 *>(b + offs[8]);
+    net->d.bg = reinterpret_cast<float *>(b + offs[9]);
+    net->d.loss_hist = reinterpret_cast<double *>(b + offs[10]);
+    net->loss_cap_n = 4096;
+    int rc = upload_params(net, params);
+    if (rc != CG_OK) return fail(rc);
+    *out = net;
+    return CG_OK;
+}
+
+int cg_net_get_params(const cg_net *net, float *params) {
+    if (!net || !params) return CG_EINVAL;
+    DeviceGuard g(net->device);
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess ||
+        cudaMemcpy(params, net->d.theta, sizeof(float) * CG_LEARN_PARAMS, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CG_ECUDA;
+    return CG_OK;
+}
+
+int cg_net_set_params(cg_net *net, const float *params) {
+    if (!net || !params || !finite_params(params)) return CG_EINVAL;
+    DeviceGuard g(net->device);
+    return upload_params(net, params);
+}
+
+void cg_net_destroy(cg_net *net) {
+    if (!net) return;
+    DeviceGuard g(net->device);
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    for (void *p : net->tallocs) cudaFree(p);
+    if (net->block) cudaFree(net->block);
+    if (net->stream) cudaStreamDestroy(net->stream);
+    delete net;
+}
+
+int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez, const float *lognu,
+                   int32_t stall_window, double stall_factor) {
+    if (!h || !net || !lognu || h->opts.precond != CG_PRECOND_LEARNED) return CG_EINVAL;
+    if (ex < 1 || ey < 1 || ez < 1) return CG_EINVAL;
+    if ((int64_t)(ex + 1) * (ey + 1) * (ez + 1) != (int64_t)h->n) return CG_EINVAL;
+    if (ex + 3 > kMaxPx) return CG_EINVAL;  // staged planes must fit shared memory
+    if (stall_window == 0) stall_window = 50;
+    if (stall_factor == 0.0) stall_factor = 0.9;
+    if (stall_window < 1 || stall_window > kMaxWindow || !(stall_factor > 0.0 && stall_factor <= 1.0))
+        return CG_EINVAL;
+    if (net->device != h->device) return CG_EINVAL;
+    for (int32_t i = 0; i < h->n; ++i)
+        if (!std::isfinite(lognu[i])) return CG_EINVAL;
+    DeviceGuard dg(h->device);
+    int rc = set_smem_limits();
+    if (rc != CG_OK) return rc;
+    learn_free(h);
+    LearnCtx *L = new (std::nothrow) LearnCtx();
+    if (!L) return CG_ENOMEM;
+    auto fail = [&](int code) {
+        free_ctx(L);
+        return code;
+    };
+    L->net = net;
+    L->G = make_geo(ex, ey, ez);
+    L->window = stall_window;
+    L->factor = stall_factor;
+    const Geo &G = L->G;
+    const int sms = sm_count(h->device);
+    L->vgrid = std::min((G.n + kVT - 1) / kVT, 4 * sms);
+    const size_t a16 = act_count(G, kCh);
+    auto &A = L->allocs;
+    const int nparts = std::max({L->vgrid, G.tiles, h->ctas});
+    if ((rc = ctx_alloc(A, &L->lognu_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->gates, a16)) ||
+        (rc = ctx_alloc(A, &L->h1, a16)) || (rc = ctx_alloc(A, &L->h2, a16)) || (rc = ctx_alloc(A, &L->k1, a16)) ||
+        (rc = ctx_alloc(A, &L->dsq, (size_t)G.n)) || (rc = ctx_alloc(A, &L->r, (size_t)G.n)) ||
+        (rc = ctx_alloc(A, &L->z, (size_t)G.n)) || (rc = ctx_alloc(A, &L->p, (size_t)G.n + 16)) ||
+        (rc = ctx_alloc(A, &L->q, (size_t)G.n)) || (rc = ctx_alloc(A, &L->partials, (size_t)3 * nparts)) ||
+        (rc = ctx_alloc(A, &L->sigma, 4)) || (rc = ctx_alloc(A, &L->counter, 4)) || (rc = ctx_alloc(A, &L->st, 1)) ||
+        (rc = ctx_alloc(A, &L->dst, 1)))
+        return fail(rc);
+    if (cudaMallocHost(&L->st_host, sizeof(FcgState)) != cudaSuccess ||
+        cudaMallocHost(&L->flags_host, 2 * sizeof(FcgFlags)) != cudaSuccess ||
+        cudaMallocHost(&L->dst_host, 2 * sizeof(DevStatus)) != cudaSuccess)
+        return fail(CG_ENOMEM);
+    if (cudaStreamCreateWithFlags(&L->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&L->t0) != cudaSuccess || cudaEventCreate(&L->t1) != cudaSuccess)
+        return fail(CG_ECUDA);
+    // log nu / 8 into the padded one-channel field (BF16)
+    std::vector<uint16_t> ln((size_t)(G.npad + kSlack), 0);
+    for (int32_t i = 0; i < G.n; ++i) {
+        const int x = i % G.nx, rest = i / G.nx, y = rest % G.ny, z = rest / G.ny;
+        const size_t pos = (size_t)(z + 1) * G.plane + (size_t)(y + 1) * G.px + (x + 1);
+        ln[pos] = bf16_bits_rne((double)lognu[i] * kLogNuScale);
+    }
+    if (cudaMemcpy(L->lognu_in, ln.data(), ln.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(CG_ECUDA);
+    dsq_kernel<<<L->vgrid, kVT, 0, h->stream>>>(G.n, h->dinv, L->dsq);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(CG_ECUDA);
+    h->learn = L;
+    return CG_OK;
+}
+
+int cg_precond_apply(cg_handle *h, const double *r, double *z) {
+    if (!h || !h->learn || !r || !z) return CG_EINVAL;
+    LearnCtx *L = h->learn;
+    DeviceGuard dg(h->device);
+    int rc = set_smem_limits();
+    if (rc != CG_OK) return rc;
+    if (cudaStreamSynchronize(L->net->stream) != cudaSuccess) return CG_ECUDA;
+    const Geo &G = L->G;
+    cudaStream_t s = h->stream;
+    launch_gates(L, L->net, s);
+    sigma_kernel<double><<<L->vgrid, kVT, 0, s>>>(G.n, r, h->dinv, L->sigma, L->counter, L->partials);
+    ConvArgs A = conv_args(G);
+    A.dsq = L->dsq;
+    A.gate = L->gates;
+    A.sigma = L->sigma;
+    A.res = r;
+    A.w = L->net->d.k1in;
+    A.out = L->h1;
+    conv1_kernel<E_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    A.res = nullptr;
+    A.in = L->h1;
+    A.w = L->net->d.k2;
+    A.out = L->h2;
+    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.in = L->h2;
+    A.w = L->net->d.k2t;
+    A.out = L->k1;
+    conv16_kernel<E_GATE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.in = L->k1;
+    A.w = L->net->d.k1t;
+    A.z = z;
+    convout_kernel<E_OUT_Z><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
+    return CG_OK;
+}
+
+int cg_learn_pairs(cg_handle *h, const double *b, const double *xstar, int32_t segment, int32_t count,
+                   float *r_out, float *e_out) {
+    if (!h || !h->learn || !b || !xstar || !r_out || !e_out || segment < 1 || count < 1) return CG_EINVAL;
+    DeviceGuard dg(h->device);
+    LearnCtx *L = h->learn;
+    cudaStream_t s = h->stream;
+    const int n = h->n;
+    if (cudaMemsetAsync(h->x_dev, 0, sizeof(double) * (size_t)n, s) != cudaSuccess) return CG_ECUDA;
+    int rc = CG_OK;
+    for (int32_t k = 0; k < count && rc == CG_OK; ++k) {
+        rc = enqueue_spmv(h, h->x_dev, L->q);
+        if (rc == CG_OK) {
+            pair_record_kernel<<<L->vgrid, kVT, 0, s>>>(n, b, xstar, h->x_dev, L->q, r_out + (size_t)k * n,
+                                                        e_out + (size_t)k * n);
+            if (cudaGetLastError() != cudaSuccess) rc = CG_ECUDA;
+        }
+        if (rc == CG_OK && k + 1 < count) rc = enqueue_fp64_solve(h, b, h->x_dev, 0.0, segment, 0);
+        if (rc == CG_OK && (k & 15) == 15 && cudaStreamSynchronize(s) != cudaSuccess) rc = CG_ECUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
+    if (rc != CG_OK) return rc;
+    const int st = h->st_host->status;
+    if (count > 1 && st != CG_OK && st != CG_ENOCONV) return st;
+    return CG_OK;
+}
+
+int cg_learn_grad(cg_net *net, const cg_learn_set *set, const int64_t *pairs, int32_t count, double *loss,
+                  float *grad) {
+    int rc = check_set(net, set);
+    if (rc != CG_OK) return rc;
+    if (!pairs || count < 1 || !loss) return CG_EINVAL;
+    for (int32_t k = 0; k < count; ++k)
+        if (pairs[k] < 0 || pairs[k] >= set->npairs) return CG_EINVAL;
+    DeviceGuard dg(net->device);
+    if ((rc = set_smem_limits()) != CG_OK) return rc;
+    const Geo &G = set->inst[0]->learn->G;
+    if ((rc = ensure_train(net, G, max_ctas(set))) != CG_OK) return rc;
+    for (int i = 0; i < set->ninst; ++i)
+        if (cudaStreamSynchronize(set->inst[i]->stream) != cudaSuccess) return CG_ECUDA;
+    cudaStream_t s = net->stream;
+    if (cudaMemsetAsync(net->d.grad, 0, sizeof(float) * CG_LEARN_PARAMS, s) != cudaSuccess ||
+        cudaMemsetAsync(net->scal, 0, sizeof(double) * 8, s) != cudaSuccess)
+        return CG_ECUDA;
+    for (int32_t k = 0; k < count; ++k) {
+        const int64_t idx = pairs[k];
+        cg_handle *h = set->inst[set->pair_inst[idx]];
+        enqueue_sample(net, h, set->r + (size_t)idx * G.n, set->e + (size_t)idx * G.n);
+    }
+    if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
+    std::vector<float> g(CG_LEARN_PARAMS);
+    double sc[8];
+    if (cudaMemcpyAsync(g.data(), net->d.grad, sizeof(float) * CG_LEARN_PARAMS, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(sc, net->scal, sizeof(sc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(net->d.grad, 0, sizeof(float) * CG_LEARN_PARAMS, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CG_ECUDA;
+    *loss = sc[2] / count;
+    if (grad) {
+        const double scale = 1.0 / ((double)G.n * count);
+        for (int j = 0; j < CG_LEARN_PARAMS; ++j) grad[j] = (float)(g[j] * scale);
+    }
+    return CG_OK;
+}
+
+int cg_learn_train(cg_net *net, const cg_learn_set *set, const int64_t *order, int32_t steps, int32_t batch,
+                   float lr, double *losses) {
+    int rc = check_set(net, set);
+    if (rc != CG_OK) return rc;
+    if (!order || steps < 1 || batch < 1 || !(lr > 0.0f) || !std::isfinite(lr)) return CG_EINVAL;
+    for (int64_t k = 0; k < (int64_t)steps * batch; ++k)
+        if (order[k] < 0 || order[k] >= set->npairs) return CG_EINVAL;
+    DeviceGuard dg(net->device);
+    if ((rc = set_smem_limits()) != CG_OK) return rc;
+    const Geo &G = set->inst[0]->learn->G;
+    if ((rc = ensure_train(net, G, max_ctas(set))) != CG_OK) return rc;
+    for (int i = 0; i < set->ninst; ++i)
+        if (cudaStreamSynchronize(set->inst[i]->stream) != cudaSuccess) return CG_ECUDA;
+    cudaStream_t s = net->stream;
+    if (cudaMemsetAsync(net->d.grad, 0, sizeof(float) * CG_LEARN_PARAMS, s) != cudaSuccess ||
+        cudaMemsetAsync(net->scal, 0, sizeof(double) * 8, s) != cudaSuccess)
+        return CG_ECUDA;
+    std::vector<double> hist;
+    for (int32_t k = 0; k < steps; ++k) {
+        for (int32_t j = 0; j < batch; ++j) {
+            const int64_t idx = order[(int64_t)k * batch + j];
+            cg_handle *h = set->inst[set->pair_inst[idx]];
+            enqueue_sample(net, h, set->r + (size_t)idx * G.n, set->e + (size_t)idx * G.n);
+        }
+        ++net->step;
+        const float bc1 = 1.0f - std::pow(0.9f, (float)net->step);
+        const float bc2 = 1.0f - std::pow(0.999f, (float)net->step);
+        const int slot = k % net->loss_cap_n;
+        adam_kernel<<<(CG_LEARN_PARAMS + kVT - 1) / kVT, kVT, 0, s>>>(
+            net->d, (float)(1.0 / ((double)G.n * batch)), lr, bc1, bc2, net->scal, 1.0 / batch, slot);
+        if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
+        if (slot == net->loss_cap_n - 1 || k == steps - 1) {
+            std::vector<double> buf(slot + 1);
+            if (cudaMemcpyAsync(buf.data(), net->d.loss_hist, sizeof(double) * (slot + 1), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return CG_ECUDA;
+            hist.insert(hist.end(), buf.begin(), buf.end());
+        }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
+    if (losses) std::memcpy(losses, hist.data(), sizeof(double) * steps);
+    return CG_OK;
+}
+
+}  // extern "C"

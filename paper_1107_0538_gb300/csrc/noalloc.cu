@@ -261,7 +261,7 @@ extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, dou
     if (A->n < 0 || A->n > CG_NOALLOC_MAX_N || A->nnz < 0 || A->nnz > (int64_t)INT32_MAX) return CG_EINVAL;
     if (!(tol >= 0.0) || !std::isfinite(tol)) return CG_EINVAL;
     if (A->n == 0) {
-        if (info) *info = cg_info{0, CG_OK, 0.0, -1.0, 0.0, 0, 0};
+        if (info) *info = cg_info{0, CG_OK, 0.0, -1.0, 0.0, 0, 0, -1, 0};
         return CG_OK;
     }
     if (!A->rowptr || !b || !x || b == x || (A->nnz > 0 && (!A->colidx || !A->vals))) return CG_EINVAL;
@@ -309,6 +309,7 @@ extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, dou
         info->kernel_ms = 0.0;
         info->launches = 1;
         info->outer = 0;
+        info->reverted_at = -1;
     }
     return s.status;
 }

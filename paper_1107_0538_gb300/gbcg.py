@@ -23,15 +23,18 @@ LIB_PATH = os.path.join(_HERE, "libgbcg.so")
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA = 0, 1, 2, 3
 CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT = 4, 5, 6, 7
 CG_MEM_HOST, CG_MEM_DEVICE = 0, 1
-CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+CG_PRECOND_NONE, CG_PRECOND_JACOBI, CG_PRECOND_LEARNED = 0, 1, 2
 CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
            "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_solve_noalloc",
            "cg_batch_create", "cg_batch_enqueue", "cg_batch_results", "cg_batch_solve",
-           "cg_batch_tune", "cg_batch_destroy")
+           "cg_batch_tune", "cg_batch_destroy", "cg_net_create", "cg_net_get_params",
+           "cg_net_set_params", "cg_net_destroy", "cg_set_learned", "cg_precond_apply", "cg_learn_pairs",
+           "cg_learn_grad", "cg_learn_train")
 CG_NOALLOC_MAX_N = 262144
+CG_LEARN_PARAMS = 7792
 
 
 class GbcgError(RuntimeError):
@@ -56,7 +59,8 @@ class cg_opts(ctypes.Structure):
 class cg_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
                 ("relres_true", ctypes.c_double), ("kernel_ms", ctypes.c_double),
-                ("launches", ctypes.c_int32), ("outer", ctypes.c_int32)]
+                ("launches", ctypes.c_int32), ("outer", ctypes.c_int32),
+                ("reverted_at", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +86,11 @@ class cg_batch_result(ctypes.Structure):
 class cg_batch_tuning(ctypes.Structure):
     _fields_ = [("inner_tol", ctypes.c_double), ("gather_tiles", ctypes.c_int32),
                 ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double)]
+
+
+class cg_learn_set(ctypes.Structure):
+    _fields_ = [("ninst", ctypes.c_int32), ("inst", ctypes.c_void_p), ("npairs", ctypes.c_int64),
+                ("pair_inst", ctypes.c_void_p), ("r", ctypes.c_void_p), ("e", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -134,6 +143,26 @@ def lib() -> ctypes.CDLL:
             L.cg_batch_tune.restype = ctypes.c_int
             L.cg_batch_destroy.argtypes = [vp]
             L.cg_batch_destroy.restype = None
+            fp = ctypes.POINTER(ctypes.c_float)
+            L.cg_net_create.argtypes = [vp, ctypes.POINTER(vp)]
+            L.cg_net_create.restype = ctypes.c_int
+            L.cg_net_get_params.argtypes = [vp, vp]
+            L.cg_net_get_params.restype = ctypes.c_int
+            L.cg_net_set_params.argtypes = [vp, vp]
+            L.cg_net_set_params.restype = ctypes.c_int
+            L.cg_net_destroy.argtypes = [vp]
+            L.cg_net_destroy.restype = None
+            L.cg_set_learned.argtypes = [vp, vp, i32, i32, i32, vp, i32, dbl]
+            L.cg_set_learned.restype = ctypes.c_int
+            L.cg_precond_apply.argtypes = [vp, vp, vp]
+            L.cg_precond_apply.restype = ctypes.c_int
+            L.cg_learn_pairs.argtypes = [vp, vp, vp, i32, i32, vp, vp]
+            L.cg_learn_pairs.restype = ctypes.c_int
+            L.cg_learn_grad.argtypes = [vp, ctypes.POINTER(cg_learn_set), vp, i32, ctypes.POINTER(dbl), vp]
+            L.cg_learn_grad.restype = ctypes.c_int
+            L.cg_learn_train.argtypes = [vp, ctypes.POINTER(cg_learn_set), vp, i32, i32, ctypes.c_float, vp]
+            L.cg_learn_train.restype = ctypes.c_int
+            del fp
             _LIB = L
     return _LIB
 
@@ -388,3 +417,146 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------ learned preconditioner
+
+def cg_net_create(params: np.ndarray) -> tuple[int, int | None]:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == CG_LEARN_PARAMS
+    h = ctypes.c_void_p()
+    rc = lib().cg_net_create(ctypes.c_void_p(p.ctypes.data), ctypes.byref(h))
+    return rc, (h.value if rc == CG_OK else None)
+
+
+def cg_net_get_params(net: int) -> tuple[int, np.ndarray]:
+    out = np.zeros(CG_LEARN_PARAMS, dtype=np.float32)
+    rc = lib().cg_net_get_params(ctypes.c_void_p(net), ctypes.c_void_p(out.ctypes.data))
+    return rc, out
+
+
+def cg_net_set_params(net: int, params: np.ndarray) -> int:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == CG_LEARN_PARAMS
+    return lib().cg_net_set_params(ctypes.c_void_p(net), ctypes.c_void_p(p.ctypes.data))
+
+
+def cg_net_destroy(net: int | None) -> None:
+    lib().cg_net_destroy(ctypes.c_void_p(net or 0))
+
+
+def cg_set_learned(h: int, net: int, ex: int, ey: int, ez: int, lognu: np.ndarray, stall_window: int = 0,
+                   stall_factor: float = 0.0) -> int:
+    ln = np.ascontiguousarray(lognu, dtype=np.float32)
+    return lib().cg_set_learned(ctypes.c_void_p(h), ctypes.c_void_p(net), int(ex), int(ey), int(ez),
+                                ctypes.c_void_p(ln.ctypes.data), int(stall_window), float(stall_factor))
+
+
+def cg_precond_apply(h: int, r_ptr: int, z_ptr: int) -> int:
+    return lib().cg_precond_apply(ctypes.c_void_p(h), ctypes.c_void_p(r_ptr), ctypes.c_void_p(z_ptr))
+
+
+def cg_learn_pairs(h: int, b_ptr: int, xstar_ptr: int, segment: int, count: int, r_ptr: int, e_ptr: int) -> int:
+    return lib().cg_learn_pairs(ctypes.c_void_p(h), ctypes.c_void_p(b_ptr), ctypes.c_void_p(xstar_ptr),
+                                int(segment), int(count), ctypes.c_void_p(r_ptr), ctypes.c_void_p(e_ptr))
+
+
+def cg_learn_grad(net: int, lset: cg_learn_set, pairs: np.ndarray) -> tuple[int, float, np.ndarray]:
+    pr = np.ascontiguousarray(pairs, dtype=np.int64)
+    loss = ctypes.c_double(0.0)
+    grad = np.zeros(CG_LEARN_PARAMS, dtype=np.float32)
+    rc = lib().cg_learn_grad(ctypes.c_void_p(net), ctypes.byref(lset), ctypes.c_void_p(pr.ctypes.data),
+                             int(pr.size), ctypes.byref(loss), ctypes.c_void_p(grad.ctypes.data))
+    return rc, loss.value, grad
+
+
+def cg_learn_train(net: int, lset: cg_learn_set, order: np.ndarray, steps: int, batch: int,
+                   lr: float) -> tuple[int, np.ndarray]:
+    od = np.ascontiguousarray(order, dtype=np.int64)
+    assert od.size >= steps * batch
+    losses = np.zeros(steps, dtype=np.float64)
+    rc = lib().cg_learn_train(ctypes.c_void_p(net), ctypes.byref(lset), ctypes.c_void_p(od.ctypes.data),
+                              int(steps), int(batch), ctypes.c_float(lr), ctypes.c_void_p(losses.ctypes.data))
+    return rc, losses
+
+
+class Net:
+    """The learned preconditioner's parameters on the current CUDA device."""
+
+    def __init__(self, params: np.ndarray):
+        rc, self.h = cg_net_create(params)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_net_create")
+
+    def params(self) -> np.ndarray:
+        rc, p = cg_net_get_params(self.h)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_net_get_params")
+        return p
+
+    def set_params(self, params: np.ndarray) -> None:
+        rc = cg_net_set_params(self.h, params)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_net_set_params")
+
+    def grad(self, lset: "LearnSet", pairs) -> tuple[float, np.ndarray]:
+        rc, loss, g = cg_learn_grad(self.h, lset.c, np.asarray(pairs))
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_learn_grad")
+        return loss, g
+
+    def train(self, lset: "LearnSet", order, steps: int, batch: int, lr: float) -> np.ndarray:
+        rc, losses = cg_learn_train(self.h, lset.c, np.asarray(order), steps, batch, lr)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_learn_train")
+        return losses
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            cg_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LearnSet:
+    """Training pairs (float32 CUDA tensors R, E of shape (npairs, n)) over
+    learned Solvers that share one grid; pair_inst gives each pair's solver."""
+
+    def __init__(self, solvers, pair_inst, R, E):
+        self._inst = (ctypes.c_void_p * len(solvers))(*[s.h for s in solvers])
+        self._pi = np.ascontiguousarray(pair_inst, dtype=np.int32)
+        assert R.shape == E.shape and R.shape[0] == self._pi.size and R.is_contiguous() and E.is_contiguous()
+        self._keep = (solvers, R, E)
+        self.c = cg_learn_set(len(solvers), ctypes.cast(self._inst, ctypes.c_void_p), int(self._pi.size),
+                              self._pi.ctypes.data, R.data_ptr(), E.data_ptr())
+
+
+def _solver_set_learned(self, net: Net, grid, lognu: np.ndarray, stall_window: int = 0,
+                        stall_factor: float = 0.0) -> None:
+    """Attaches the learned preconditioner (grid: object with ex, ey, ez)."""
+    rc = cg_set_learned(self.h, net.h, grid.ex, grid.ey, grid.ez, lognu, stall_window, stall_factor)
+    if rc != CG_OK:
+        raise GbcgError(rc, "cg_set_learned")
+    self._net = net
+
+
+def _solver_precond_apply(self, r, z) -> None:
+    rc = cg_precond_apply(self.h, r.data_ptr(), z.data_ptr())
+    if rc != CG_OK:
+        raise GbcgError(rc, "cg_precond_apply")
+
+
+def _solver_learn_pairs(self, b, xstar, segment: int, count: int, R, E) -> None:
+    rc = cg_learn_pairs(self.h, b.data_ptr(), xstar.data_ptr(), segment, count, R.data_ptr(), E.data_ptr())
+    if rc != CG_OK:
+        raise GbcgError(rc, "cg_learn_pairs")
+
+
+Solver.set_learned = _solver_set_learned
+Solver.precond_apply = _solver_precond_apply
+Solver.learn_pairs = _solver_learn_pairs

@@ -57,13 +57,15 @@ int main(void) {
   F(cg_opts, debug_phantom_arrivals) F(cg_opts, vectors_in_memory)
   F(cg_opts, inner_values) F(cg_opts, inner_tol) F(cg_opts, max_outer) F(cg_opts, max_inner)
   F(cg_info, iters) F(cg_info, status) F(cg_info, relres) F(cg_info, relres_true)
-  F(cg_info, kernel_ms) F(cg_info, launches) F(cg_info, outer)
+  F(cg_info, kernel_ms) F(cg_info, launches) F(cg_info, outer) F(cg_info, reverted_at) F(cg_info, reserved)
   F(cg_plan, n) F(cg_plan, nnz) F(cg_plan, ctas) F(cg_plan, threads) F(cg_plan, tiles)
   F(cg_plan, tile_nnz) F(cg_plan, stages) F(cg_plan, smem_bytes) F(cg_plan, lanes_per_row)
   F(cg_plan, l2_evict_first) F(cg_plan, reg_rows) F(cg_plan, window_tiles) F(cg_plan, device_bytes)
   F(cg_batch_result, iters) F(cg_batch_result, outer) F(cg_batch_result, status) F(cg_batch_result, reserved)
   F(cg_batch_result, relres)
   F(cg_batch_tuning, inner_tol) F(cg_batch_tuning, gather_tiles) F(cg_batch_tuning, trials) F(cg_batch_tuning, best_ms)
+  F(cg_learn_set, ninst) F(cg_learn_set, inst) F(cg_learn_set, npairs) F(cg_learn_set, pair_inst)
+  F(cg_learn_set, r) F(cg_learn_set, e)
   printf("\\"sizes\\": [%zu, %zu, %zu, %zu]}", sizeof(cg_csr), sizeof(cg_opts), sizeof(cg_info), sizeof(cg_plan));
   return 0;
 }
@@ -71,7 +73,8 @@ int main(void) {
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     c = json.loads(subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout)
-    for T in (gbcg.cg_csr, gbcg.cg_opts, gbcg.cg_info, gbcg.cg_plan, gbcg.cg_batch_result, gbcg.cg_batch_tuning):
+    for T in (gbcg.cg_csr, gbcg.cg_opts, gbcg.cg_info, gbcg.cg_plan, gbcg.cg_batch_result, gbcg.cg_batch_tuning,
+              gbcg.cg_learn_set):
         for name, ctype in T._fields_:
             off, size = c[f"{T.__name__}.{name}"]
             assert getattr(T, name).offset == off, (T.__name__, name)
@@ -189,3 +192,28 @@ def test_batch_rejects_bad_arguments_without_gpu():
     assert gbcg.cg_batch_create(broken, None, None)[0] == gbcg.CG_EINVAL
     assert gbcg.lib().cg_batch_create(None, 0, None, None, None) == gbcg.CG_EINVAL
     gbcg.cg_batch_destroy(None)
+
+
+def test_learned_entry_points_reject_bad_arguments_without_gpu():
+    L = gbcg.lib()
+    bad = np.full(gbcg.CG_LEARN_PARAMS, np.nan, dtype=np.float32)
+    h = ctypes.c_void_p()
+    assert L.cg_net_create(None, ctypes.byref(h)) == gbcg.CG_EINVAL
+    assert L.cg_net_create(ctypes.c_void_p(bad.ctypes.data), ctypes.byref(h)) == gbcg.CG_EINVAL
+    assert L.cg_net_create(ctypes.c_void_p(bad.ctypes.data), None) == gbcg.CG_EINVAL
+    assert L.cg_net_get_params(None, None) == gbcg.CG_EINVAL
+    assert L.cg_net_set_params(None, None) == gbcg.CG_EINVAL
+    gbcg.cg_net_destroy(None)
+    assert gbcg.cg_set_learned(0, 0, 4, 4, 4, np.zeros(125)) == gbcg.CG_EINVAL
+    assert gbcg.cg_precond_apply(0, 8, 16) == gbcg.CG_EINVAL
+    assert gbcg.cg_learn_pairs(0, 8, 16, 4, 4, 32, 64) == gbcg.CG_EINVAL
+    s = gbcg.cg_learn_set(0, None, 0, None, None, None)
+    assert gbcg.cg_learn_grad(0, s, np.zeros(1, np.int64))[0] == gbcg.CG_EINVAL
+    assert gbcg.cg_learn_train(0, s, np.zeros(1, np.int64), 1, 1, 1e-3)[0] == gbcg.CG_EINVAL
+    # the learned preconditioner is FP64-only
+    o = gbcg.cg_opts_default()
+    o.precond = gbcg.CG_PRECOND_LEARNED
+    o.inner_values = gbcg.CG_VALUES_FP32
+    A = problems.cube_uniform(2).A
+    c, keep = gbcg.host_csr(A)
+    assert gbcg.cg_create(c, o, None)[0] == gbcg.CG_EINVAL
