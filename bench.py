@@ -45,6 +45,8 @@ def parse_args():
                     help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
     ap.add_argument("--batched-full", action="store_true",
                     help="only measure the full batched workload (256 systems, edges 20..80, 4 rhs)")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="only train the learned preconditioner and measure it (50^3 and unseen 100^3)")
     return ap.parse_args()
 
 
@@ -273,6 +275,95 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sam
     return out
 
 
+def measure_learned(ninst: int = 40, per: int = 500, seg: int = 8, batch: int = 8, lr: float = 1e-3,
+                    reps: int = 3) -> dict:
+    """The learned preconditioner end to end on the GPU: training pairs from
+    restarted FP64 CG on ninst random 50^3 instances (contrast 1e3, seeds
+    10000+), one epoch of Adam through the project's kernels, then flexible CG
+    with the network against FP64 CG and Jacobi-PCG on the 50^3 workload and
+    on an unseen 100^3 instance (seed 20000), to rel. residual 1e-8."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"workload": f"train: {ninst} q1-50^3 blob instances x {per} (residual, error) pairs from restarted "
+                       f"FP64 CG (segments of {seg}); test: flexible CG to rel. residual {TOL:g}"}
+    t0 = time.perf_counter()
+    train = [problems.learn_instance(50, 10000 + i) for i in range(ninst)]
+    out["instances_s"] = round(time.perf_counter() - t0, 2)
+    net = gbcg.Net(problems.learn_init_params())
+    solvers = []
+    for inst in train:
+        s = gbcg.Solver(inst.A, precond=gbcg.CG_PRECOND_LEARNED)
+        s.set_learned(net, inst.grid, inst.lognu.astype(np.float32))
+        solvers.append(s)
+    n = train[0].A.n
+    R = torch.empty((ninst * per, n), dtype=torch.float32, device=dev)
+    E = torch.empty_like(R)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, (inst, s) in enumerate(zip(train, solvers)):
+        s.learn_pairs(torch.from_numpy(inst.b).to(dev), torch.from_numpy(inst.xstar).to(dev), seg, per,
+                      R[k * per:(k + 1) * per], E[k * per:(k + 1) * per])
+    torch.cuda.synchronize()
+    out["pairs"] = ninst * per
+    out["pairs_s"] = round(time.perf_counter() - t0, 2)
+    pinst = np.repeat(np.arange(ninst), per)
+    lset = gbcg.LearnSet(solvers, pinst, R, E)
+    held = np.arange(0, len(pinst), max(1, len(pinst) // 256))
+    loss0, _ = net.grad(lset, held)
+    steps = len(pinst) // batch
+    order = (problems.splitmix64(77, steps * batch) % np.uint64(len(pinst))).astype(np.int64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.train(lset, order, steps, batch, lr)
+    torch.cuda.synchronize()
+    out["train"] = {"steps": steps, "batch": batch, "lr": lr, "epochs": 1, "s": round(time.perf_counter() - t0, 2),
+                    "held_out_loss_before": round(loss0, 5), "held_out_loss_after": round(net.grad(lset, held)[0], 5),
+                    "held": f"{len(held)} training pairs, every {max(1, len(pinst) // 256)}th"}
+    del R, E, lset
+    for s in solvers:
+        s.close()
+    torch.cuda.empty_cache()
+
+    def run(A, b, mk):
+        s = mk()
+        bt = torch.from_numpy(b).to(dev)
+        x = torch.zeros_like(bt)
+        s.solve(bt, x, TOL)
+        ts, info = [], None
+        for _ in range(reps):
+            x.zero_()
+            torch.cuda.synchronize()
+            info = s.solve(bt, x, TOL)
+            ts.append(info.kernel_ms)
+        s.close()
+        return {"ms_per_solve": round(statistics.median(ts), 3), "iters": info.iters, "status": info.status,
+                "relres_true": info.relres_true, "reverted_at": info.reverted_at}
+
+    def learned_solver(A, grid, lognu):
+        def mk():
+            s = gbcg.Solver(A, precond=gbcg.CG_PRECOND_LEARNED)
+            s.set_learned(net, grid, lognu.astype(np.float32))
+            return s
+        return mk
+
+    c2 = problems.cube_blobs(50)
+    test100 = problems.learn_instance(100, 20000)
+    for key, A, b, grid, lognu in (("q1_50cube_c2", c2.A, c2.b, c2.grid, problems.node_log_nu(c2.grid, c2.nu)),
+                                   ("q1_100cube_unseen", test100.A, test100.b, test100.grid, test100.lognu)):
+        res = {"fp64_cg": run(A, b, lambda: gbcg.Solver(A)),
+               "jacobi_pcg": run(A, b, lambda: gbcg.Solver(A, precond=gbcg.CG_PRECOND_JACOBI)),
+               "learned_fcg": run(A, b, learned_solver(A, grid, lognu))}
+        lf = res["learned_fcg"]
+        lf["speedup_vs_fp64_cg"] = round(res["fp64_cg"]["ms_per_solve"] / lf["ms_per_solve"], 3)
+        lf["speedup_vs_jacobi_pcg"] = round(res["jacobi_pcg"]["ms_per_solve"] / lf["ms_per_solve"], 3)
+        lf["iters_vs_jacobi_pcg"] = round(lf["iters"] / max(res["jacobi_pcg"]["iters"], 1), 3)
+        out[key] = res
+    net.close()
+    return out
+
+
 def run_gbcg(args) -> None:
     import torch
     import torch.distributed as dist
@@ -446,6 +537,12 @@ def run_gbcg(args) -> None:
         line["gpu_launches"] += 0  # extras are outside the timed region
         # --------------------------------------- batched solves (mini config)
         line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
+        # ------------------------------------------ learned preconditioner
+        line["learned"] = measure_learned()
+        lf = line["learned"]["q1_50cube_c2"]["learned_fcg"]
+        forms["learned_fcg"] = {"ms_per_solve": lf["ms_per_solve"], "iters": lf["iters"],
+                                "relres_true": lf["relres_true"], "reverted_at": lf["reverted_at"],
+                                "speedup_vs_fp64_cg": round(ms_per_step / lf["ms_per_solve"], 3)}
 
         # ----------------------------------------------- CPU oracle baseline
         if rank == 0 and world == 1:
@@ -465,6 +562,13 @@ def run_gbcg(args) -> None:
 
 def main():
     args = parse_args()
+    if args.learned_only:
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1107_0538_gb300 import gbcg
+        gbcg.lib()
+        print(json.dumps({"learned": measure_learned()}), flush=True)
+        return
     if args.batched_full:
         import torch
         torch.cuda.set_device(0)

@@ -11,14 +11,14 @@
 //   a zero tail; a 16-channel BF16 activation is 32 bytes per position.
 //
 // A convolution is an implicit GEMM on the tensor cores (mma.sync m16n8k16,
-// BF16 in, FP32 accumulate): an M-tile is 16 consecutive positions of one
-// padded xy-plane, so each of the 27 taps reads 16 consecutive staged rows
-// (a constant shift of the tile); halo positions compute garbage that is
-// never stored, so every store goes to an interior node and the zero halo is
-// never overwritten.  A CTA (4 warps) takes kTL positions of kTZ planes; its
-// input (kTZ + 2 planes x kTL + 2 px + 2 positions) is staged once into
-// shared memory with a bank-conflict-free swizzle of the two 16-byte halves
-// of each row.
+// BF16 in, FP32 accumulate).  A CTA (8 warps) computes a brick of 16 x 8 x 4
+// output nodes; an M-tile is one x-row of the brick (16 consecutive nodes),
+// so each of the 27 taps reads 16 consecutive rows of the staged input (a
+// constant shift).  The brick's input with its one-node halo (18 x 10 x 6
+// positions, 35 KB for 16 channels) is staged once into shared memory with a
+// bank-conflict-free swizzle of the two 16-byte halves of each row; outputs
+// past the grid (ragged bricks) are computed and dropped, so every store
+// goes to an interior node and the zero halo is never overwritten.
 //
 // Flexible CG runs as a CUDA graph of kUnroll iterations of seven kernels
 // (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, p update, SpMV + p.q,
@@ -51,15 +51,17 @@ constexpr int kOffW1 = 0, kOffW2 = kCh * kTaps, kOffWg = kOffW2 + kCh * kCh * kT
 static_assert(kOffBg + kCh == CG_LEARN_PARAMS, "parameter layout");
 constexpr float kLogNuScale = 0.125f;
 
-constexpr int kTL = 64;          // padded xy positions per conv tile (4 M-tiles)
-constexpr int kTZ = 4;           // planes per conv tile (one warp each)
-constexpr int kCT = 128;         // threads of a conv CTA
-constexpr int kMTiles = kTL / 16;
-constexpr int kSlack = kTL + 64; // zero positions after the padded grid
-constexpr int kMaxPx = 522;      // staged rows must fit shared memory
+constexpr int kBX = 16, kBY = 8, kBZ = 4;                 // output brick of a conv CTA
+constexpr int kSX = kBX + 2, kSY = kBY + 2, kSZ = kBZ + 2;   // staged brick with its halo
+constexpr int kStaged = kSX * kSY * kSZ;                     // 1080 positions
+constexpr int kRows = kBY * kBZ;                             // M-tiles (x-rows) per brick
+constexpr int kCT = 256;                                     // threads of a conv CTA (8 warps)
+constexpr int kMTiles = kRows / (kCT / 32);                  // M-tiles per warp
+constexpr int kSlack = 64;       // zero positions after the padded grid
 constexpr int kVT = 256;         // threads of the vector kernels
 constexpr int kMaxWindow = 128;
 constexpr int kUnroll = 6;       // iterations per graph launch
+static_assert(kMTiles == 4, "warp w owns rows 4 (w & 1) .. + 3 of plane w / 2");
 
 constexpr int kModeLearned = 0, kModeJacobi = 1;
 
@@ -68,9 +70,7 @@ struct Geo {
     int nx, ny, nz;       // nodes per axis
     int px, py, pz;       // padded extents
     int plane;            // px * py
-    int s_begin, s_len;   // interior xy range of a padded plane
-    int xy_chunks, z_chunks, tiles;
-    int rl;               // staged positions per plane: kTL + 2 px + 2
+    int bx, by, bz, tiles;
     int n;                // nodes
     long long npad;       // px py pz
 };
@@ -84,24 +84,23 @@ Geo make_geo(int ex, int ey, int ez) {
     G.py = G.ny + 2;
     G.pz = G.nz + 2;
     G.plane = G.px * G.py;
-    G.s_begin = G.px + 1;
-    G.s_len = (G.ny - 1) * G.px + G.nx;
-    G.xy_chunks = (G.s_len + kTL - 1) / kTL;
-    G.z_chunks = (G.nz + kTZ - 1) / kTZ;
-    G.tiles = G.xy_chunks * G.z_chunks;
-    G.rl = kTL + 2 * G.px + 2;
+    G.bx = (G.nx + kBX - 1) / kBX;
+    G.by = (G.ny + kBY - 1) / kBY;
+    G.bz = (G.nz + kBZ - 1) / kBZ;
+    G.tiles = G.bx * G.by * G.bz;
     G.n = G.nx * G.ny * G.nz;
     G.npad = (long long)G.px * G.py * G.pz;
     return G;
 }
 
-size_t conv16_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTaps * kCh * kCh * 2; }
-size_t conv1_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 2 + 16; }
-size_t convout_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTaps * kCh * 2; }
-size_t wgrad16_smem(const Geo &G) { return (size_t)(kTZ + 2) * G.rl * 32 + (size_t)kTZ * kTL * 32; }
-size_t wgrad1_smem(const Geo &G) {
-    return ((size_t)(kTZ + 2) * G.rl * 2 + 15) / 16 * 16 + 16 + (size_t)kTZ * kTL * 32 + 4 * 16 * 32 * 4;
-}
+constexpr size_t kStage16 = (size_t)kStaged * 32;
+constexpr size_t kStage1 = ((size_t)kStaged * 2 + 15) / 16 * 16;
+constexpr size_t kDyTile = (size_t)kBX * kRows * 32;
+size_t conv16_smem(const Geo &) { return kStage16 + (size_t)kTaps * kCh * kCh * 2; }
+size_t conv1_smem(const Geo &) { return kStage1; }
+size_t convout_smem(const Geo &) { return kStage16; }
+size_t wgrad16_smem(const Geo &) { return kStage16 + kDyTile; }
+size_t wgrad1_smem(const Geo &) { return kStage1 + kDyTile + (size_t)(kCT / 32) * 16 * 32 * 4; }
 
 // ---------------------------------------------------------------- device
 __device__ __forceinline__ int tap_dx(int t) { return t % 3 - 1; }
@@ -148,72 +147,65 @@ __device__ __forceinline__ uint32_t row_addr(uint32_t base, int R, int h) {
     return base + (uint32_t)R * 32u + ((uint32_t)(h ^ ((R >> 2) & 1)) << 4);
 }
 
-// Interior test of a padded position and its node index (-1 outside).
-__device__ __forceinline__ int node_of(const Geo &G, long long pos) {
-    const int z = (int)(pos / G.plane);
-    const int rem = (int)(pos - (long long)z * G.plane);
-    const int y = rem / G.px, x = rem - y * G.px;
-    if (x < 1 || x > G.nx || y < 1 || y > G.ny || z < 1 || z > G.nz) return -1;
-    return (x - 1) + G.nx * ((y - 1) + G.ny * (z - 1));
+// A brick: origin (x0, y0, z0) of its outputs in node coordinates.
+struct Brick {
+    int x0, y0, z0;
+};
+__device__ __forceinline__ Brick brick_of(const Geo &G, int tile) {
+    const int tx = tile % G.bx, rest = tile / G.bx;
+    return Brick{tx * kBX, (rest % G.by) * kBY, (rest / G.by) * kBZ};
 }
 
-// Output position of row `row` (0..15) of M-tile m in warp w's plane;
-// returns the padded position, or -1 if it is not an interior node.
-__device__ __forceinline__ long long out_pos(const Geo &G, int s0, int z0, int w, int m, int row) {
-    const int zi = z0 + w;                 // interior plane index
-    const int s = s0 + 16 * m + row;       // padded xy index
-    if (zi >= G.nz || s >= G.s_begin + G.s_len) return -1;
-    const int x = s % G.px;
-    if (x < 1 || x > G.nx) return -1;
-    return (long long)(zi + 1) * G.plane + s;
+// Staged position (xs, ys, zs) of a brick is padded node (x0 + xs, y0 + ys,
+// z0 + zs); its row (ys, zs) exists in the padded grid when
+// y0 + ys < py and z0 + zs < pz (rows past it only feed dropped outputs).
+__device__ __forceinline__ bool staged_row(const Geo &G, const Brick &B, int ys, int zs, long long &pos0) {
+    const int py = B.y0 + ys, pz = B.z0 + zs;
+    pos0 = (long long)pz * G.plane + (long long)py * G.px + B.x0;
+    return py < G.py && pz < G.pz;
 }
 
-// Stages the 16-channel input of a tile (kTZ + 2 planes x rl positions).
-__device__ __forceinline__ void stage16(const Geo &G, const __nv_bfloat16 *src, unsigned char *sm, int s0,
-                                        int z0) {
-    const int per_plane = G.rl * 2;
-    const int total = (kTZ + 2) * per_plane;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int lp = idx / per_plane, rem = idx - lp * per_plane;
-        const int j = rem >> 1, h = rem & 1;
-        const int R = lp * G.rl + j;
+// Stages the 16-channel input of a brick (rows of 18 positions, 36 chunks of 16 bytes).
+__device__ __forceinline__ void stage16(const Geo &G, const Brick &B, const __nv_bfloat16 *src, unsigned char *sm) {
+    constexpr int kChunks = kSX * 2;
+    for (int c = threadIdx.x; c < kSY * kSZ * kChunks; c += blockDim.x) {
+        const int row = c / kChunks, k = c - row * kChunks;
+        const int xs = k >> 1, h = k & 1;
+        const int ys = row % kSY, zs = row / kSY;
+        const int R = row * kSX + xs;
         unsigned char *dst = sm + R * 32 + ((h ^ ((R >> 2) & 1)) << 4);
-        const int zin = z0 + lp;
-        if (zin < G.pz) {
-            const long long pos = (long long)zin * G.plane + (s0 - G.px - 1) + j;
-            cp_async16(dst, src + pos * kCh + h * 8);
-        } else {
-            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-        }
+        long long pos0;
+        if (staged_row(G, B, ys, zs, pos0)) cp_async16(dst, src + (pos0 + xs) * kCh + h * 8);
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
-// One-channel input of a tile, as BF16 (kTZ + 2 planes x rl positions):
-// from a padded BF16 field, or from a node-order vector v scaled by
-// dsq[i] * scale (the network input s_hat = D^-1/2 r / sigma).
-template <class VT>
-__device__ __forceinline__ void stage1(const Geo &G, const __nv_bfloat16 *src, const VT *v, const double *dsq,
-                                       double scale, uint16_t *sm, int s0, int z0) {
-    const int total = (kTZ + 2) * G.rl;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int lp = idx / G.rl, j = idx - lp * G.rl;
-        const int zin = z0 + lp;
-        uint16_t val = 0;
-        if (zin < G.pz) {
-            const long long pos = (long long)zin * G.plane + (s0 - G.px - 1) + j;
-            if (src) {
-                val = reinterpret_cast<const uint16_t *>(src)[pos];
-            } else {
-                const int i = node_of(G, pos);
-                if (i >= 0) {
-                    const float f = (float)((double)v[i] * dsq[i] * scale);
-                    __nv_bfloat16 b = __float2bfloat16_rn(f);
-                    val = *reinterpret_cast<uint16_t *>(&b);
-                }
-            }
-        }
-        sm[idx] = val;
+// One-channel input of a brick (a padded BF16 field).
+__device__ __forceinline__ void stage1(const Geo &G, const Brick &B, const __nv_bfloat16 *src, uint16_t *sm) {
+    for (int c = threadIdx.x; c < kStaged; c += blockDim.x) {
+        const int row = c / kSX, xs = c - row * kSX;
+        const int ys = row % kSY, zs = row / kSY;
+        long long pos0;
+        sm[c] = staged_row(G, B, ys, zs, pos0) ? reinterpret_cast<const uint16_t *>(src)[pos0 + xs] : (uint16_t)0;
     }
+}
+
+// Output row r of a warp's M-tile m: node coordinates and validity.
+struct OutRow {
+    int x, y, z;
+    bool ok;
+};
+__device__ __forceinline__ OutRow out_row(const Geo &G, const Brick &B, int w, int m, int r) {
+    OutRow o{B.x0 + r, B.y0 + 4 * (w & 1) + m, B.z0 + (w >> 1), false};
+    o.ok = o.x < G.nx && o.y < G.ny && o.z < G.nz;
+    return o;
+}
+__device__ __forceinline__ long long padded_pos(const Geo &G, int x, int y, int z) {
+    return (long long)(z + 1) * G.plane + (long long)(y + 1) * G.px + (x + 1);
+}
+// Staged row index of the A operand of warp w, M-tile m, for tap offsets (dx, dy, dz).
+__device__ __forceinline__ int a_row(int w, int m, int dx, int dy, int dz) {
+    return (((w >> 1) + 1 + dz) * kSY + (4 * (w & 1) + m + 1 + dy)) * kSX + 1 + dx;
 }
 
 // ------------------------------------------------------- solver state
@@ -237,8 +229,6 @@ struct FcgFlags {
 struct ConvArgs {
     Geo G;
     const __nv_bfloat16 *in;     // padded input (16 channels, or 1 channel for conv1)
-    const double *res;           // conv1: node-order FP64 input (when in == nullptr)
-    const float *resf;           // conv1: node-order FP32 input (when in == nullptr and res == nullptr)
     const double *dsq;           // 1 / sqrt(diag A)
     const __nv_bfloat16 *w;      // packed weights of this convolution
     const float *bias;           // E_SIGMOID
@@ -254,8 +244,8 @@ struct ConvArgs {
     const double *q;             // E_OUT_FCG: A p of the last step
     const double *dinv;          // Jacobi fallback
     double *partials;
-    FcgState *st;                // solver state (nullptr: always run, scale from sigma_inv below)
-    const double *sigma;         // apply: {sigma, 1/sigma} for the input scale and the output
+    FcgState *st;                // solver state (nullptr: always run; conv1 scales by sigma[1] if set)
+    const double *sigma;         // apply: {sigma, 1/sigma}: conv1 output scale, conv_out output scale
 };
 
 enum { E_STORE = 0, E_GATE = 1, E_GATE_PRE = 2, E_BWD_GATE = 3, E_SIGMOID = 4 };
@@ -265,21 +255,44 @@ __device__ __forceinline__ bool conv_skip(const FcgState *st) {
     return st && (st->done || st->mode != kModeLearned);
 }
 
-// 16-channel output of one warp's M-tiles: acc[m][nb][4] (rows g, g+8; columns 2t4, 2t4+1 of n-block nb).
+// Gates of a warp's output rows, loaded ahead of the MMA loop: gv[m][hrow][nb]
+// (two channels each), zero for dropped rows.
 template <int EPI>
-__device__ __forceinline__ void store16(const ConvArgs &A, int s0, int z0, int w, float (&acc)[kMTiles][2][4]) {
+__device__ __forceinline__ void load_gates(const ConvArgs &A, const Brick &B, int w,
+                                           uint32_t (&gv)[kMTiles][2][2]) {
+    if (EPI != E_GATE && EPI != E_GATE_PRE && EPI != E_BWD_GATE) return;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int m = 0; m < kMTiles; ++m)
+#pragma unroll
+        for (int hrow = 0; hrow < 2; ++hrow) {
+            const OutRow o = out_row(A.G, B, w, m, g + 8 * hrow);
+            const long long pos = padded_pos(A.G, o.x, o.y, o.z);
+#pragma unroll
+            for (int nb = 0; nb < 2; ++nb)
+                gv[m][hrow][nb] = o.ok ? __ldg(reinterpret_cast<const unsigned int *>(A.gate + pos * kCh + nb * 8 + 2 * t4))
+                                       : 0u;
+        }
+}
+
+// 16-channel output of one warp's M-tiles: acc[m][nb][4] (rows g, g+8;
+// columns 2t4, 2t4+1 of n-block nb), scaled by oscale first.
+template <int EPI>
+__device__ __forceinline__ void store16(const ConvArgs &A, const Brick &B, int w, float (&acc)[kMTiles][2][4],
+                                        const uint32_t (&gvv)[kMTiles][2][2], float oscale) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
 #pragma unroll
     for (int m = 0; m < kMTiles; ++m) {
 #pragma unroll
         for (int hrow = 0; hrow < 2; ++hrow) {
-            const long long pos = out_pos(A.G, s0, z0, w, m, g + 8 * hrow);
-            if (pos < 0) continue;
+            const OutRow o = out_row(A.G, B, w, m, g + 8 * hrow);
+            if (!o.ok) continue;
+            const long long pos = padded_pos(A.G, o.x, o.y, o.z);
 #pragma unroll
             for (int nb = 0; nb < 2; ++nb) {
                 const int ch = nb * 8 + 2 * t4;
                 const long long e = pos * kCh + ch;
-                float v0 = acc[m][nb][2 * hrow], v1 = acc[m][nb][2 * hrow + 1];
+                float v0 = acc[m][nb][2 * hrow] * oscale, v1 = acc[m][nb][2 * hrow + 1] * oscale;
                 if (EPI == E_SIGMOID) {
                     v0 = 1.0f / (1.0f + __expf(-(v0 + A.bias[ch])));
                     v1 = 1.0f / (1.0f + __expf(-(v1 + A.bias[ch + 1])));
@@ -287,7 +300,7 @@ __device__ __forceinline__ void store16(const ConvArgs &A, int s0, int z0, int w
                 } else if (EPI == E_STORE) {
                     *reinterpret_cast<uint32_t *>(A.out + e) = pack_bf16(v0, v1);
                 } else {
-                    const float2 gv = unpack_bf16(*reinterpret_cast<const uint32_t *>(A.gate + e));
+                    const float2 gv = unpack_bf16(gvv[m][hrow][nb]);
                     if (EPI == E_GATE_PRE) *reinterpret_cast<uint32_t *>(A.pre + e) = pack_bf16(v0, v1);
                     if (EPI == E_BWD_GATE) {
                         const float2 pv = unpack_bf16(*reinterpret_cast<const uint32_t *>(A.pre + e));
@@ -307,15 +320,16 @@ __device__ __forceinline__ void store16(const ConvArgs &A, int s0, int z0, int w
 // ------------------------------------------------- 16 -> 16 convolution
 // y[o, p] = sum_{t, c} K[t][o][c] x[c, p + off(t)], K packed [27][16][16].
 template <int EPI>
-__global__ void __launch_bounds__(kCT) conv16_kernel(ConvArgs A) {
+__global__ void __launch_bounds__(kCT, 3) conv16_kernel(ConvArgs A) {
     if (conv_skip(A.st)) return;
     extern __shared__ __align__(128) unsigned char sm[];
     const Geo &G = A.G;
-    unsigned char *sw = sm + (size_t)(kTZ + 2) * G.rl * 32;
-    const int tile = blockIdx.x;
-    const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
-    const int z0 = (tile / G.xy_chunks) * kTZ;
-    stage16(G, A.in, sm, s0, z0);
+    unsigned char *sw = sm + kStage16;
+    const Brick B = brick_of(G, blockIdx.x);
+    stage16(G, B, A.in, sm);
+    const int w = threadIdx.x >> 5;
+    uint32_t gv[kMTiles][2][2];
+    load_gates<EPI>(A, B, w, gv);
     // weights: row (t, o) of 32 bytes, swizzled like the input
     for (int idx = threadIdx.x; idx < kTaps * kCh * 2; idx += blockDim.x) {
         const int R = idx >> 1, h = idx & 1;
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(kCT) conv16_kernel(ConvArgs A) {
     }
     cp_async_wait_all();
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t in_base = smem_u32(sm), w_base = smem_u32(sw);
     float acc[kMTiles][2][4];
 #pragma unroll
@@ -332,42 +346,38 @@ __global__ void __launch_bounds__(kCT) conv16_kernel(ConvArgs A) {
         for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[m][nb][k] = 0.0f;
-    const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
+    const int a_r = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
     const int b_o = (lane & 7) + ((lane >> 4) << 3), b_half = (lane >> 3) & 1;
-#pragma unroll 3
+#pragma unroll
     for (int t = 0; t < kTaps; ++t) {
         uint32_t b[4];
         ldsm_x4(b, row_addr(w_base, t * kCh + b_o, b_half));
-        const int plane_row = (w + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px;
 #pragma unroll
         for (int m = 0; m < kMTiles; ++m) {
             uint32_t a[4];
-            ldsm_x4(a, row_addr(in_base, plane_row + 16 * m + a_row, a_half));
+            ldsm_x4(a, row_addr(in_base, a_row(w, m, tap_dx(t), tap_dy(t), tap_dz(t)) + a_r, a_half));
             mma_bf16(acc[m][0], a, b[0], b[1]);
             mma_bf16(acc[m][1], a, b[2], b[3]);
         }
     }
-    store16<EPI>(A, s0, z0, w, acc);
+    store16<EPI>(A, B, w, acc, gv, 1.0f);
 }
 
 // --------------------------------------------------- 1 -> 16 convolution
 // y[o, p] = sum_t K[o][t] x[p + off(t)], K packed [16][32] (taps 27..31 zero):
 // the taps are the GEMM's K dimension, gathered from the staged plane.
-template <int EPI, class VT>
+template <int EPI>
 __global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
     if (conv_skip(A.st)) return;
     extern __shared__ __align__(128) unsigned char sm[];
     const Geo &G = A.G;
     uint16_t *xs = reinterpret_cast<uint16_t *>(sm);
-    const int tile = blockIdx.x;
-    const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
-    const int z0 = (tile / G.xy_chunks) * kTZ;
-    double scale = 1.0;
-    if (!A.in) scale = A.st ? A.st->sigma_inv : A.sigma[1];
-    const VT *vin;
-    if constexpr (std::is_same<VT, double>::value) vin = A.res;
-    else vin = A.resf;
-    stage1<VT>(G, A.in, vin, A.dsq, scale, xs, s0, z0);
+    const Brick B = brick_of(G, blockIdx.x);
+    // the input is D^-1/2 r (flexible CG, apply): scale the output by 1/sigma
+    const float oscale = A.st ? (float)A.st->sigma_inv : (A.sigma ? (float)A.sigma[1] : 1.0f);
+    stage1(G, B, A.in, xs);
+    uint32_t gv[kMTiles][2][2];
+    load_gates<EPI>(A, B, threadIdx.x >> 5, gv);
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
     // B fragments (whole K = 32 taps): b[ks][nb][2]
@@ -378,8 +388,8 @@ __global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
 #pragma unroll
         for (int nb = 0; nb < 2; ++nb) {
             const int o = nb * 8 + g;
-            b[ks][nb][0] = wk[(o * kTapsPad + ks * 16 + 2 * t4) >> 1];
-            b[ks][nb][1] = wk[(o * kTapsPad + ks * 16 + 8 + 2 * t4) >> 1];
+            b[ks][nb][0] = __ldg(wk + ((o * kTapsPad + ks * 16 + 2 * t4) >> 1));
+            b[ks][nb][1] = __ldg(wk + ((o * kTapsPad + ks * 16 + 8 + 2 * t4) >> 1));
         }
     // staged offsets of the taps this lane gathers: k = ks*16 + {2t4, 2t4+1, 2t4+8, 2t4+9}
     int off[2][4];
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
             const int t = ks * 16 + 2 * t4 + (u & 1) + (u >> 1) * 8;
             live[ks][u] = t < kTaps;
             const int tt = t < kTaps ? t : kCentre;
-            off[ks][u] = (1 + tap_dz(tt)) * G.rl + G.px + 1 + tap_dx(tt) + tap_dy(tt) * G.px;
+            off[ks][u] = a_row(w, 0, tap_dx(tt), tap_dy(tt), tap_dz(tt));
         }
     float acc[kMTiles][2][4];
 #pragma unroll
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
         for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[m][nb][k] = 0.0f;
-        const int base = w * G.rl + 16 * m + g;
+        const int base = m * kSX + g;   // M-tile m is the next staged row
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks) {
             uint16_t v[2][4];
@@ -417,7 +427,7 @@ __global__ void __launch_bounds__(kCT) conv1_kernel(ConvArgs A) {
             mma_bf16(acc[m][1], a, b[ks][1][0], b[ks][1][1]);
         }
     }
-    store16<EPI>(A, s0, z0, w, acc);
+    store16<EPI>(A, B, w, acc, gv, oscale);
 }
 
 // ----------------------------------------------- deterministic reductions
@@ -438,11 +448,13 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double *sred) {
 }
 
 // Publishes this CTA's partials (thread 0 holds them); true in every thread
-// of the last CTA to arrive, which then sums all partials in CTA order into
-// tot (thread 0) and resets the counter.
+// of the last CTA to arrive, which then sums all partials into tot (warp 0)
+// and resets the counter.  Every thread of that CTA adds a fixed strided
+// subset (loads in flight together), then cta_sum combines them: a fixed
+// order for a given grid, so the totals are reproducible.
 template <int NV>
 __device__ __forceinline__ bool last_cta_totals(double (&v)[NV], double *partials, unsigned int *counter,
-                                                double (&tot)[NV], int *sflag) {
+                                                double (&tot)[NV], int *sflag, double *sred) {
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) partials[(size_t)j * gridDim.x + blockIdx.x] = v[j];
@@ -452,17 +464,19 @@ __device__ __forceinline__ bool last_cta_totals(double (&v)[NV], double *partial
     __syncthreads();
     if (!*sflag) return false;
     __threadfence();
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x < 32) {
-        const int G = (int)gridDim.x;
+    const int G = (int)gridDim.x;
+    double acc[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            double s = 0.0;
-            for (int m = lane; m < G; m += 32) s += __ldcg(partials + (size_t)j * G + m);
-            tot[j] = warp_sum(s);
-        }
-        if (threadIdx.x == 0) *counter = 0u;
+    for (int j = 0; j < NV; ++j) acc[j] = 0.0;
+#pragma unroll 4
+    for (int m = threadIdx.x; m < G; m += blockDim.x) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) acc[j] += __ldcg(partials + (size_t)j * G + m);
     }
+    cta_sum<NV>(acc, sred);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) tot[j] = acc[j];
+    if (threadIdx.x == 0) *counter = 0u;
     return true;
 }
 
@@ -483,62 +497,68 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     if (st && st->done) return;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double sred[2 * 32];
+    __shared__ float su[kRows * kBX];
     __shared__ int sflag;
     const Geo &G = A.G;
     const bool learned = !st || st->mode == kModeLearned;
     double dzr = 0.0, dzq = 0.0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
     if (learned) {
-        unsigned char *sw = sm + (size_t)(kTZ + 2) * G.rl * 32;
-        const int tile = blockIdx.x;
-        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
-        const int z0 = (tile / G.xy_chunks) * kTZ;
-        stage16(G, A.in, sm, s0, z0);
-        for (int idx = threadIdx.x; idx < kTaps * 2; idx += blockDim.x)
-            cp_async16(sw + idx * 16, A.w + (size_t)idx * 8);
+        const Brick B = brick_of(G, blockIdx.x);
+        stage16(G, B, A.in, sm);
+        // B operand (one real output column): this lane's words of every tap,
+        // zero in the lanes of the other seven columns
+        uint32_t bw[kTaps][2];
+        const uint32_t *wk = reinterpret_cast<const uint32_t *>(A.w);
+#pragma unroll
+        for (int t = 0; t < kTaps; ++t) {
+            bw[t][0] = g == 0 ? __ldg(wk + ((t * kCh + 2 * t4) >> 1)) : 0u;
+            bw[t][1] = g == 0 ? __ldg(wk + ((t * kCh + 8 + 2 * t4) >> 1)) : 0u;
+        }
         cp_async_wait_all();
         __syncthreads();
         const uint32_t in_base = smem_u32(sm);
-        const uint32_t *wk = reinterpret_cast<const uint32_t *>(sw);
         float acc[kMTiles][4];
 #pragma unroll
         for (int m = 0; m < kMTiles; ++m)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
-        const int a_row = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
-#pragma unroll 3
+        const int a_r = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
+#pragma unroll
         for (int t = 0; t < kTaps; ++t) {
-            const uint32_t b0 = g == 0 ? wk[(t * kCh + 2 * t4) >> 1] : 0u;
-            const uint32_t b1 = g == 0 ? wk[(t * kCh + 8 + 2 * t4) >> 1] : 0u;
-            const int plane_row = (w + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px;
 #pragma unroll
             for (int m = 0; m < kMTiles; ++m) {
                 uint32_t a[4];
-                ldsm_x4(a, row_addr(in_base, plane_row + 16 * m + a_row, a_half));
-                mma_bf16(acc[m], a, b0, b1);
+                ldsm_x4(a, row_addr(in_base, a_row(w, m, tap_dx(t), tap_dy(t), tap_dz(t)) + a_r, a_half));
+                mma_bf16(acc[m], a, bw[t][0], bw[t][1]);
             }
         }
+        // u of the brick through shared memory, then one output per thread
         if (t4 == 0) {
-            const double sigma = EPI == E_OUT_U ? 1.0 : (st ? st->sigma : A.sigma[0]);
 #pragma unroll
             for (int m = 0; m < kMTiles; ++m)
 #pragma unroll
-                for (int hr = 0; hr < 2; ++hr) {
-                    const long long pos = out_pos(G, s0, z0, w, m, g + 8 * hr);
-                    if (pos < 0) continue;
-                    const int i = node_of(G, pos);
-                    const float u = acc[m][2 * hr];
-                    if (EPI == E_OUT_U) {
-                        A.u[i] = u;
-                    } else {
-                        const double zi = sigma * A.dsq[i] * (double)u;
-                        A.z[i] = zi;
-                        if (EPI == E_OUT_FCG) {
-                            dzr = fma(zi, A.r[i], dzr);
-                            dzq = fma(zi, A.q[i], dzq);
-                        }
-                    }
+                for (int hr = 0; hr < 2; ++hr)
+                    su[((w >> 1) * kBY + 4 * (w & 1) + m) * kBX + g + 8 * hr] = acc[m][2 * hr];
+        }
+        __syncthreads();
+        const double sigma = EPI == E_OUT_U ? 1.0 : (st ? st->sigma : A.sigma[0]);
+        for (int idx = threadIdx.x; idx < kRows * kBX; idx += blockDim.x) {
+            const int row = idx / kBX, xr = idx - row * kBX;
+            const int x = B.x0 + xr, y = B.y0 + row % kBY, z = B.z0 + row / kBY;
+            if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
+            const int i = x + G.nx * (y + G.ny * z);
+            const float u = su[idx];
+            if (EPI == E_OUT_U) {
+                A.u[i] = u;
+            } else {
+                const double zi = sigma * A.dsq[i] * (double)u;
+                A.z[i] = zi;
+                if (EPI == E_OUT_FCG) {
+                    dzr = fma(zi, A.r[i], dzr);
+                    dzq = fma(zi, A.q[i], dzq);
                 }
+            }
         }
     } else {
         const int n = G.n;
@@ -552,7 +572,7 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     if (EPI != E_OUT_FCG) return;
     double v[2] = {dzr, dzq}, tot[2];
     cta_sum<2>(v, sred);
-    if (!last_cta_totals<2>(v, A.partials, &st->counter, tot, &sflag)) return;
+    if (!last_cta_totals<2>(v, A.partials, &st->counter, tot, &sflag, sred)) return;
     if (threadIdx.x == 0) {
         const double zr = tot[0], zq = tot[1];
         st->zr = zr;
@@ -581,7 +601,9 @@ struct VecArgs {
     int n;
     FcgState *st;
     double *x, *r, *z, *p, *q;
-    const double *dinv;
+    const double *dinv, *dsq;
+    const int32_t *pidx;      // padded position of each node
+    __nv_bfloat16 *s_in;      // padded network input D^-1/2 r (BF16)
     double *partials;
 };
 
@@ -611,12 +633,13 @@ __global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
         x[i] = fma(alpha, V.p[i], x[i]);
         const double ri = fma(-alpha, V.q[i], V.r[i]);
         V.r[i] = ri;
+        V.s_in[V.pidx[i]] = __float2bfloat16_rn((float)(ri * V.dsq[i]));
         rr = fma(ri, ri, rr);
         rdr = fma(ri * V.dinv[i], ri, rdr);
     }
     double v[2] = {rr, rdr}, tot[2];
     cta_sum<2>(v, sred);
-    if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag)) return;
+    if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag, sred)) return;
     // warp 0 of the last CTA: the residual-norm window for the stall test
     const int lane = threadIdx.x & 31;
     if (threadIdx.x >= 32) return;
@@ -657,13 +680,16 @@ __global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
 }
 
 // ---------------------------------------------------------- SpMV kernels
-struct EpiSetupL {      // r = b - A x; r.r, b.b, r.D^-1 r
-    const double *b, *dinv;
+struct EpiSetupL {      // r = b - A x, s_in = D^-1/2 r; r.r, b.b, r.D^-1 r
+    const double *b, *dinv, *dsq;
+    const int32_t *pidx;
+    __nv_bfloat16 *s_in;
     double *r;
     double rr = 0.0, bb = 0.0, rdr = 0.0;
     __device__ __forceinline__ void row(int i, double ax, int) {
         const double bi = b[i], ri = bi - ax;
         r[i] = ri;
+        s_in[pidx[i]] = __float2bfloat16_rn((float)(ri * dsq[i]));
         rr = fma(ri, ri, rr);
         bb = fma(bi, bi, bb);
         rdr = fma(ri * dinv[i], ri, rdr);
@@ -696,7 +722,7 @@ enum { S_SETUP = 0, S_Q = 1, S_TRUE = 2 };
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgState *st, const double *vec,
-                                                                double *partials) {
+                                                                double *partials, VecArgs V) {
     if (MODE == S_Q && st->done) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Smem S = carve_smem(smem_raw);
@@ -705,7 +731,7 @@ __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgStat
     Pipe pipe;
     double v[3] = {0.0, 0.0, 0.0};
     if (MODE == S_SETUP) {
-        EpiSetupL e{st->b, P.dinv, P.r};
+        EpiSetupL e{st->b, P.dinv, V.dsq, V.pidx, V.s_in, P.r};
         (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, vec, e, true);
         v[0] = e.rr;
         v[1] = e.bb;
@@ -722,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgStat
     drain<double, double>(P, S, pipe, vec);
     block_sum<3>(v, S);
     double tot[3];
-    if (!last_cta_totals<3>(v, partials, &st->counter, tot, &sflag)) return;
+    if (!last_cta_totals<3>(v, partials, &st->counter, tot, &sflag, S.red)) return;
     if (threadIdx.x != 0) return;
     if (MODE == S_SETUP) {
         st->rr = tot[0];
@@ -780,13 +806,8 @@ struct TrainArgs {
     double *t;                // D^-1/2 v (SpMV input)
     const double *y;          // A t
     __nv_bfloat16 *du;        // padded, 1 channel: A_hat v (n times the loss gradient)
+    const int32_t *pidx;      // padded position of each node
 };
-
-__device__ __forceinline__ long long padded_of(const Geo &G, int i) {
-    const int x = i % G.nx, rest = i / G.nx;
-    const int y = rest % G.ny, z = rest / G.ny;
-    return (long long)(z + 1) * G.plane + (long long)(y + 1) * G.px + (x + 1);
-}
 
 // sigma = rms(D^-1/2 v) over a node-order vector (FP32 pair or FP64 residual).
 template <class VT>
@@ -801,7 +822,7 @@ __global__ void __launch_bounds__(kVT) sigma_kernel(int n, const VT *v, const do
     }
     double a[1] = {acc}, tot[1];
     cta_sum<1>(a, sred);
-    if (!last_cta_totals<1>(a, partials, counter, tot, &sflag)) return;
+    if (!last_cta_totals<1>(a, partials, counter, tot, &sflag, sred)) return;
     if (threadIdx.x == 0) {
         const double sigma = sqrt(tot[0] / (double)n);
         scal[0] = sigma;
@@ -813,8 +834,7 @@ __global__ void __launch_bounds__(kVT) sigma_kernel(int n, const VT *v, const do
 __global__ void __launch_bounds__(kVT) pair_input_kernel(TrainArgs T) {
     const double sinv = T.scal[1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.G.n; i += gridDim.x * blockDim.x) {
-        const long long pos = padded_of(T.G, i);
-        T.shat[pos] = __float2bfloat16_rn((float)((double)T.r[i] * T.dsq[i] * sinv));
+        T.shat[T.pidx[i]] = __float2bfloat16_rn((float)((double)T.r[i] * T.dsq[i] * sinv));
         T.ehat[i] = (float)((double)T.e[i] / T.dsq[i] * sinv);
     }
 }
@@ -836,11 +856,11 @@ __global__ void __launch_bounds__(kVT) loss_kernel(TrainArgs T) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < T.G.n; i += gridDim.x * blockDim.x) {
         const double wi = T.dsq[i] * T.y[i];
         acc = fma((double)T.v[i], wi, acc);
-        T.du[padded_of(T.G, i)] = __float2bfloat16_rn((float)wi);
+        T.du[T.pidx[i]] = __float2bfloat16_rn((float)wi);
     }
     double a[1] = {acc}, tot[1];
     cta_sum<1>(a, sred);
-    if (!last_cta_totals<1>(a, T.partials, T.counter, tot, &sflag)) return;
+    if (!last_cta_totals<1>(a, T.partials, T.counter, tot, &sflag, sred)) return;
     if (threadIdx.x == 0) T.scal[2] += 0.5 * tot[0] / (double)T.G.n;
 }
 
@@ -864,28 +884,42 @@ struct WgArgs {
     int add;                   // 0: part = ..., 1: part += ...
 };
 
-// Stages the gradient tile dy (kTZ planes x kTL positions, no halo).
-__device__ __forceinline__ void stage_dy(const Geo &G, const __nv_bfloat16 *dy, unsigned char *sdy, int s0, int z0) {
-    for (int idx = threadIdx.x; idx < kTZ * kTL * 2; idx += blockDim.x) {
-        const int lp = idx / (kTL * 2), rem = idx - lp * (kTL * 2);
-        const int j = rem >> 1, h = rem & 1;
-        const int R = lp * kTL + j;
+// Stages the gradient brick dy (16 x 8 x 4 positions, no halo): row
+// (yl, zl) at kBX (zl * kBY + yl), swizzled like the input.
+__device__ __forceinline__ void stage_dy(const Geo &G, const Brick &B, const __nv_bfloat16 *dy, unsigned char *sdy) {
+    constexpr int kChunks = kBX * 2;
+    for (int c = threadIdx.x; c < kRows * kChunks; c += blockDim.x) {
+        const int row = c / kChunks, k = c - row * kChunks;
+        const int xr = k >> 1, h = k & 1;
+        const int yl = row % kBY, zl = row / kBY;
+        const int R = row * kBX + xr;
         unsigned char *dst = sdy + R * 32 + ((h ^ ((R >> 2) & 1)) << 4);
-        const int zin = z0 + 1 + lp;
-        if (zin < G.pz) cp_async16(dst, dy + ((long long)zin * G.plane + s0 + j) * kCh + h * 8);
-        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        long long pos0;
+        // positions past the grid in x would read the next row: they are zeroed
+        if (staged_row(G, B, yl + 1, zl + 1, pos0) && B.x0 + xr < G.nx)
+            cp_async16(dst, dy + (pos0 + 1 + xr) * kCh + h * 8);
+        else
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
+}
+
+// Staged input row of dy row `row` (= zl * kBY + yl), shifted by a tap.
+__device__ __forceinline__ int x_row(int row, int dx, int dy, int dz) {
+    const int yl = row % kBY, zl = row / kBY;
+    return ((zl + 1 + dz) * kSY + (yl + 1 + dy)) * kSX + 1 + dx;
 }
 
 // G[o][c][t] = sum_p dy[o, p] x[c, p + off(t)] for 16-channel dy and x: a
 // GEMM over positions (M = o, N = c, K = p) per tap; warp w owns taps
-// w, w + 4, ...  Persistent over tiles; the CTA's sums go to part[blockIdx.x].
+// w, w + 8, ...  Persistent over bricks; the CTA's sums go to part[blockIdx.x].
+// dy is zero off the interior nodes, so dropped positions add nothing.
 __global__ void __launch_bounds__(kCT) wgrad16_kernel(WgArgs W) {
     extern __shared__ __align__(128) unsigned char sm[];
     const Geo &G = W.G;
-    unsigned char *sdy = sm + (size_t)(kTZ + 2) * G.rl * 32;
+    unsigned char *sdy = sm + kStage16;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
-    constexpr int kMaxT = (kTaps + 3) / 4;
+    constexpr int kWarpsC = kCT / 32;
+    constexpr int kMaxT = (kTaps + kWarpsC - 1) / kWarpsC;
     float acc[kMaxT][2][4];
 #pragma unroll
     for (int i = 0; i < kMaxT; ++i)
@@ -897,23 +931,20 @@ __global__ void __launch_bounds__(kCT) wgrad16_kernel(WgArgs W) {
     const int a_pos = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
     const int b_pos = (lane & 7) + (((lane >> 3) & 1) << 3), b_half = lane >> 4;
     for (int tile = blockIdx.x; tile < G.tiles; tile += gridDim.x) {
-        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
-        const int z0 = (tile / G.xy_chunks) * kTZ;
-        stage16(G, W.x, sm, s0, z0);
-        stage_dy(G, W.dy, sdy, s0, z0);
+        const Brick B = brick_of(G, tile);
+        stage16(G, B, W.x, sm);
+        stage_dy(G, B, W.dy, sdy);
         cp_async_wait_all();
         __syncthreads();
-        for (int ks = 0; ks < kTZ * kMTiles; ++ks) {
-            const int lp = ks / kMTiles, m = ks - lp * kMTiles;
+        for (int row = 0; row < kRows; ++row) {
             uint32_t a[4];
-            ldsm_x4_t(a, row_addr(dy_base, lp * kTL + 16 * m + a_pos, a_half));
+            ldsm_x4_t(a, row_addr(dy_base, row * kBX + a_pos, a_half));
 #pragma unroll
             for (int i = 0; i < kMaxT; ++i) {
-                const int t = w + 4 * i;
+                const int t = w + kWarpsC * i;
                 if (t < kTaps) {
-                    const int row = (lp + 1 + tap_dz(t)) * G.rl + G.px + 1 + tap_dx(t) + tap_dy(t) * G.px + 16 * m;
                     uint32_t b[4];
-                    ldsm_x4_t(b, row_addr(in_base, row + b_pos, b_half));
+                    ldsm_x4_t(b, row_addr(in_base, x_row(row, tap_dx(t), tap_dy(t), tap_dz(t)) + b_pos, b_half));
                     mma_bf16(acc[i][0], a, b[0], b[1]);
                     mma_bf16(acc[i][1], a, b[2], b[3]);
                 }
@@ -924,7 +955,7 @@ __global__ void __launch_bounds__(kCT) wgrad16_kernel(WgArgs W) {
     float *part = W.part + (size_t)blockIdx.x * CG_LEARN_PARAMS + W.off;
 #pragma unroll
     for (int i = 0; i < kMaxT; ++i) {
-        const int t = w + 4 * i;
+        const int t = w + kWarpsC * i;
         if (t >= kTaps) continue;
 #pragma unroll
         for (int nb = 0; nb < 2; ++nb)
@@ -940,14 +971,14 @@ __global__ void __launch_bounds__(kCT) wgrad16_kernel(WgArgs W) {
 // G[o][t] = sum_p dy[o, p] x[p + off(t)] for 16-channel dy and a 1-channel
 // x (taps are the GEMM's N dimension, 4 blocks of 8; "tap" 27 multiplies
 // by one and gives the channel sums of dy when bias_off >= 0).  Warps split
-// the positions and add their sums in shared memory at the end.
+// the rows of a brick and add their sums in shared memory at the end.
 __global__ void __launch_bounds__(kCT) wgrad1_kernel(WgArgs W) {
     extern __shared__ __align__(128) unsigned char sm[];
     const Geo &G = W.G;
+    constexpr int kWarpsC = kCT / 32;
     uint16_t *xs = reinterpret_cast<uint16_t *>(sm);
-    const size_t xs_bytes = ((size_t)(kTZ + 2) * G.rl * 2 + 15) / 16 * 16 + 16;
-    unsigned char *sdy = sm + xs_bytes;
-    float *sacc = reinterpret_cast<float *>(sdy + (size_t)kTZ * kTL * 32);   // [4 warps][16][32]
+    unsigned char *sdy = sm + kStage1;
+    float *sacc = reinterpret_cast<float *>(sdy + kDyTile);   // [warps][16][32]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
     float acc[4][4];
 #pragma unroll
@@ -956,33 +987,29 @@ __global__ void __launch_bounds__(kCT) wgrad1_kernel(WgArgs W) {
         for (int k = 0; k < 4; ++k) acc[nb][k] = 0.0f;
     const uint32_t dy_base = smem_u32(sdy);
     const int a_pos = (lane & 7) + ((lane >> 4) << 3), a_half = (lane >> 3) & 1;
-    // staged offset of tap nb*8 + g (taps past 26: none)
-    int toff[4];
     int tkind[4];   // 0 tap, 1 constant one, 2 zero
+    int tt_of[4];
 #pragma unroll
     for (int nb = 0; nb < 4; ++nb) {
         const int t = nb * 8 + g;
         tkind[nb] = t < kTaps ? 0 : (t == kTaps && W.bias_off >= 0 ? 1 : 2);
-        const int tt = t < kTaps ? t : kCentre;
-        toff[nb] = (1 + tap_dz(tt)) * G.rl + G.px + 1 + tap_dx(tt) + tap_dy(tt) * G.px;
+        tt_of[nb] = t < kTaps ? t : kCentre;
     }
     for (int tile = blockIdx.x; tile < G.tiles; tile += gridDim.x) {
-        const int s0 = G.s_begin + (tile % G.xy_chunks) * kTL;
-        const int z0 = (tile / G.xy_chunks) * kTZ;
-        stage1<float>(G, W.x, nullptr, nullptr, 1.0, xs, s0, z0);
-        stage_dy(G, W.dy, sdy, s0, z0);
+        const Brick B = brick_of(G, tile);
+        stage1(G, B, W.x, xs);
+        stage_dy(G, B, W.dy, sdy);
         cp_async_wait_all();
         __syncthreads();
-        for (int ks = w; ks < kTZ * kMTiles; ks += 4) {
-            const int lp = ks / kMTiles, m = ks - lp * kMTiles;
+        for (int row = w; row < kRows; row += kWarpsC) {
             uint32_t a[4];
-            ldsm_x4_t(a, row_addr(dy_base, lp * kTL + 16 * m + a_pos, a_half));
-            const int base = lp * G.rl + 16 * m + 2 * t4;
+            ldsm_x4_t(a, row_addr(dy_base, row * kBX + a_pos, a_half));
 #pragma unroll
             for (int nb = 0; nb < 4; ++nb) {
                 uint32_t b0, b1;
                 if (tkind[nb] == 0) {
-                    const uint16_t *xp = xs + base + toff[nb];
+                    const int tt = tt_of[nb];
+                    const uint16_t *xp = xs + x_row(row, tap_dx(tt), tap_dy(tt), tap_dz(tt)) + 2 * t4;
                     b0 = pack_raw(xp[0], xp[1]);
                     b1 = pack_raw(xp[8], xp[9]);
                 } else if (tkind[nb] == 1) {
@@ -995,7 +1022,7 @@ __global__ void __launch_bounds__(kCT) wgrad1_kernel(WgArgs W) {
         }
         __syncthreads();
     }
-    // sum the four warps' accumulators: sacc[w][o][tap]
+    // sum the warps' accumulators: sacc[w][o][tap]
 #pragma unroll
     for (int nb = 0; nb < 4; ++nb)
 #pragma unroll
@@ -1009,7 +1036,7 @@ __global__ void __launch_bounds__(kCT) wgrad1_kernel(WgArgs W) {
         const int o = idx >> 5, tap = idx & 31;
         float s = 0.0f;
 #pragma unroll
-        for (int ww = 0; ww < 4; ++ww) s += sacc[(ww * 16 + o) * 32 + tap];
+        for (int ww = 0; ww < kWarpsC; ++ww) s += sacc[(ww * 16 + o) * 32 + tap];
         float *dst = nullptr;
         if (tap < kTaps) dst = part + W.off + o * kTaps + tap;
         else if (tap == kTaps && W.bias_off >= 0) dst = part + W.bias_off + o;
@@ -1086,6 +1113,13 @@ __global__ void __launch_bounds__(kVT) pair_record_kernel(int n, const double *b
     }
 }
 
+// s_in = D^-1/2 r at the padded positions (the network input before 1/sigma).
+__global__ void __launch_bounds__(kVT) scatter_s_kernel(int n, const double *r, const double *dsq,
+                                                        const int32_t *pidx, __nv_bfloat16 *s_in) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        s_in[pidx[i]] = __float2bfloat16_rn((float)(r[i] * dsq[i]));
+}
+
 __global__ void __launch_bounds__(kVT) dsq_kernel(int n, const double *dinv, double *dsq) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dsq[i] = sqrt(dinv[i]);
 }
@@ -1123,6 +1157,8 @@ struct LearnCtx {
     double factor = 0.9;
     std::vector<void *> allocs;
     __nv_bfloat16 *lognu_in = nullptr, *gates = nullptr, *h1 = nullptr, *h2 = nullptr, *k1 = nullptr;
+    __nv_bfloat16 *s_in = nullptr;   // padded D^-1/2 r (network input)
+    int32_t *pidx = nullptr;         // padded position of each node
     double *dsq = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *partials = nullptr, *sigma = nullptr;
     unsigned int *counter = nullptr;
@@ -1173,12 +1209,18 @@ int set_smem_limits() {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return CG_ECUDA;
     cudaError_t e = cudaSuccess;
+    // every kernel of a solve asks for the same (maximal) shared-memory
+    // carveout, so that consecutive kernels never wait for the SMs to be
+    // reconfigured
     auto set = [&](const void *f) {
         cudaFuncAttributes fa{};
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      optin - (int)fa.sharedSizeBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
     };
     set((const void *)conv16_kernel<E_STORE>);
     set((const void *)conv16_kernel<E_GATE>);
@@ -1193,6 +1235,12 @@ int set_smem_limits() {
     set((const void *)fcg_spmv_kernel<S_Q>);
     set((const void *)fcg_spmv_kernel<S_TRUE>);
     set((const void *)spmv_store_kernel);
+    set((const void *)conv1_kernel<E_GATE>);
+    set((const void *)conv1_kernel<E_SIGMOID>);
+    set((const void *)conv1_kernel<E_GATE_PRE>);
+    set((const void *)conv1_kernel<E_BWD_GATE>);
+    set((const void *)fcg_p_kernel);
+    set((const void *)fcg_xr_kernel);
     if (e != cudaSuccess) return CG_ECUDA;
     done = 1;
     return CG_OK;
@@ -1211,7 +1259,7 @@ void launch_gates(const LearnCtx *L, const cg_net *net, cudaStream_t s) {
     A.w = net->d.kgin;
     A.bias = net->d.bg;
     A.out = L->gates;
-    conv1_kernel<E_SIGMOID, double><<<L->G.tiles, kCT, conv1_smem(L->G), s>>>(A);
+    conv1_kernel<E_SIGMOID><<<L->G.tiles, kCT, conv1_smem(L->G), s>>>(A);
 }
 
 Params learn_params(cg_handle *h, LearnCtx *L) {
@@ -1223,6 +1271,22 @@ Params learn_params(cg_handle *h, LearnCtx *L) {
     return P;
 }
 
+VecArgs vec_args(cg_handle *h, LearnCtx *L) {
+    VecArgs V{};
+    V.n = L->G.n;
+    V.st = L->st;
+    V.r = L->r;
+    V.z = L->z;
+    V.p = L->p;
+    V.q = L->q;
+    V.dinv = h->dinv;
+    V.dsq = L->dsq;
+    V.pidx = L->pidx;
+    V.s_in = L->s_in;
+    V.partials = L->partials;
+    return V;
+}
+
 // One flexible-CG iteration: seven launches.
 void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     const Geo &G = L->G;
@@ -1231,15 +1295,13 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.st = L->st;
     A.dsq = L->dsq;
     A.gate = L->gates;
-    // h1 = g * C1(s_hat), s_hat = D^-1/2 r / sigma staged from r
-    A.in = nullptr;
-    A.res = L->r;
+    // h1 = g * C1(D^-1/2 r) / sigma
+    A.in = L->s_in;
     A.w = net->d.k1in;
     A.out = L->h1;
-    conv1_kernel<E_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    conv1_kernel<E_GATE><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
     // h2 = C2(h1)
     A.in = L->h1;
-    A.res = nullptr;
     A.w = net->d.k2;
     A.out = L->h2;
     conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
@@ -1257,18 +1319,10 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.dinv = h->dinv;
     A.partials = L->partials;
     convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
-    VecArgs V{};
-    V.n = G.n;
-    V.st = L->st;
-    V.r = L->r;
-    V.z = L->z;
-    V.p = L->p;
-    V.q = L->q;
-    V.dinv = h->dinv;
-    V.partials = L->partials;
+    const VecArgs V = vec_args(h, L);
     fcg_p_kernel<<<L->vgrid, kVT, 0, s>>>(V);
     Params P = learn_params(h, L);
-    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, L->p, L->partials);
+    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, L->p, L->partials, V);
     fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
 }
 
@@ -1373,6 +1427,7 @@ void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
     T.t = net->t;
     T.y = net->y;
     T.du = net->du;
+    T.pidx = L->pidx;
     const int vg = net->vgrid;
     sigma_kernel<float><<<vg, kVT, 0, s>>>(G.n, r, h->dinv, net->scal, net->counter, net->partials);
     pair_input_kernel<<<vg, kVT, 0, s>>>(T);
@@ -1384,7 +1439,7 @@ void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
     A.w = net->d.k1in;
     A.out = net->h1;
     A.pre = net->a1;
-    conv1_kernel<E_GATE_PRE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    conv1_kernel<E_GATE_PRE><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
     A.in = net->h1;
     A.w = net->d.k2;
     A.out = net->h2;
@@ -1416,7 +1471,7 @@ void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
     A.pre = net->kpre;
     A.dg = net->dg;
     A.dg_add = 0;
-    conv1_kernel<E_BWD_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
+    conv1_kernel<E_BWD_GATE><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
     W.dy = net->k1;
     W.x = net->du;
     W.off = kOffW1;
@@ -1525,7 +1580,8 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
     int launches = 0;
     launch_gates(L, net, s);
     Params P = learn_params(h, L);
-    fcg_spmv_kernel<S_SETUP><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials);
+    fcg_spmv_kernel<S_SETUP><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials,
+                                                                   vec_args(h, L));
     launches += 2;
     if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
     // graph launches, two in flight; each body advances the iteration count
@@ -1555,7 +1611,8 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
     if (h->opts.true_residual) {
-        fcg_spmv_kernel<S_TRUE><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials);
+        fcg_spmv_kernel<S_TRUE><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials,
+                                                                      vec_args(h, L));
         ++launches;
     }
     e = cudaEventRecord(L->t1, s);
@@ -1665,7 +1722,6 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
     if (!h || !net || !lognu || h->opts.precond != CG_PRECOND_LEARNED) return CG_EINVAL;
     if (ex < 1 || ey < 1 || ez < 1) return CG_EINVAL;
     if ((int64_t)(ex + 1) * (ey + 1) * (ez + 1) != (int64_t)h->n) return CG_EINVAL;
-    if (ex + 3 > kMaxPx) return CG_EINVAL;  // staged planes must fit shared memory
     if (stall_window == 0) stall_window = 50;
     if (stall_factor == 0.0) stall_factor = 0.9;
     if (stall_window < 1 || stall_window > kMaxWindow || !(stall_factor > 0.0 && stall_factor <= 1.0))
@@ -1694,6 +1750,7 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
     auto &A = L->allocs;
     const int nparts = std::max({L->vgrid, G.tiles, h->ctas});
     if ((rc = ctx_alloc(A, &L->lognu_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->gates, a16)) ||
+        (rc = ctx_alloc(A, &L->s_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->pidx, (size_t)G.n)) ||
         (rc = ctx_alloc(A, &L->h1, a16)) || (rc = ctx_alloc(A, &L->h2, a16)) || (rc = ctx_alloc(A, &L->k1, a16)) ||
         (rc = ctx_alloc(A, &L->dsq, (size_t)G.n)) || (rc = ctx_alloc(A, &L->r, (size_t)G.n)) ||
         (rc = ctx_alloc(A, &L->z, (size_t)G.n)) || (rc = ctx_alloc(A, &L->p, (size_t)G.n + 16)) ||
@@ -1712,12 +1769,15 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
         return fail(CG_ECUDA);
     // log nu / 8 into the padded one-channel field (BF16)
     std::vector<uint16_t> ln((size_t)(G.npad + kSlack), 0);
+    std::vector<int32_t> pidx((size_t)G.n);
     for (int32_t i = 0; i < G.n; ++i) {
         const int x = i % G.nx, rest = i / G.nx, y = rest % G.ny, z = rest / G.ny;
         const size_t pos = (size_t)(z + 1) * G.plane + (size_t)(y + 1) * G.px + (x + 1);
         ln[pos] = bf16_bits_rne((double)lognu[i] * kLogNuScale);
+        pidx[i] = (int32_t)pos;
     }
-    if (cudaMemcpy(L->lognu_in, ln.data(), ln.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(L->lognu_in, ln.data(), ln.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(L->pidx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(CG_ECUDA);
     dsq_kernel<<<L->vgrid, kVT, 0, h->stream>>>(G.n, h->dinv, L->dsq);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(CG_ECUDA);
@@ -1736,15 +1796,15 @@ int cg_precond_apply(cg_handle *h, const double *r, double *z) {
     cudaStream_t s = h->stream;
     launch_gates(L, L->net, s);
     sigma_kernel<double><<<L->vgrid, kVT, 0, s>>>(G.n, r, h->dinv, L->sigma, L->counter, L->partials);
+    scatter_s_kernel<<<L->vgrid, kVT, 0, s>>>(G.n, r, L->dsq, L->pidx, L->s_in);
     ConvArgs A = conv_args(G);
     A.dsq = L->dsq;
     A.gate = L->gates;
     A.sigma = L->sigma;
-    A.res = r;
+    A.in = L->s_in;
     A.w = L->net->d.k1in;
     A.out = L->h1;
-    conv1_kernel<E_GATE, double><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
-    A.res = nullptr;
+    conv1_kernel<E_GATE><<<G.tiles, kCT, conv1_smem(G), s>>>(A);
     A.in = L->h1;
     A.w = L->net->d.k2;
     A.out = L->h2;
