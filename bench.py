@@ -43,10 +43,13 @@ def parse_args():
     ap.add_argument("--impl", choices=["gbcg", "reference"], default="gbcg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
-    ap.add_argument("--batched-full", action="store_true",
-                    help="only measure the full batched workload (256 systems, edges 20..80, 4 rhs)")
-    ap.add_argument("--learned-only", action="store_true",
-                    help="only train the learned preconditioner and measure it (50^3 and unseen 100^3)")
+    ap.add_argument("--section", choices=["spmv", "forms", "batched", "batched_full", "learned", "learned_iter"],
+                    help="run one extra section alone and print its JSON: the 100^3 SpMV roofline, the "
+                         "other forms on the 50^3 workload, the 64-system batch, the full 256-system batch, "
+                         "the learned preconditioner (training and tests), or the time per flexible-CG "
+                         "iteration with an untrained network at 50^3 and 100^3")
+    ap.add_argument("--batched-full", action="store_true", help="same as --section batched_full")
+    ap.add_argument("--learned-only", action="store_true", help="same as --section learned")
     return ap.parse_args()
 
 
@@ -80,19 +83,39 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+# Sources whose content fixes each kernel's code and launch plan: a capture in
+# profiles/ncu_traffic.txt counts only while their digest is unchanged.
+_COMMON = ["cg_device.cuh", "layout.h"]
+KERNEL_SOURCES = {
+    "cg_solve_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
+    "spmv_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
+    "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
+    "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
+    "conv16_kernel": ["learn.cu"] + _COMMON,
+    "convout_kernel": ["learn.cu"] + _COMMON,
+    "conv1_kernel": ["learn.cu"] + _COMMON,
+    "fcg_spmv_kernel": ["learn.cu", "plan.h"] + _COMMON,
+}
+
+
+def source_digest(kernel: str) -> str:
+    """sha256 (first 16 hex digits) of the kernel's source files in order."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1107_0538_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic(kernel: str) -> dict | None:
     """DRAM bytes per launch of a kernel from the committed ncu capture summary
     (profiles/ncu_traffic.txt), if it was taken on the current kernel source
     (digest match), else None."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    src = os.path.join(ROOT, "paper_1107_0538_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        h.update(open(os.path.join(src, f), "rb").read())
-    digest = h.hexdigest()[:16]
+    digest = source_digest(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
@@ -195,7 +218,7 @@ def run_reference(args) -> None:
 def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sample: int) -> dict:
     """Batched mixed-precision solves of nsys uneven Q1 boxes x 4 source-current
     right-hand sides in one persistent launch; optional autotuning; CUDA graph
-    capture of the enqueue; error of sampled pairs against the FP64 oracle."""
+    capture of the enqueue; error of sampled pairs against a tight FP64 GPU solve."""
     import torch
 
     from paper_1107_0538_gb300 import gbcg, problems
@@ -257,20 +280,24 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sam
         bsg.close()
     except Exception as exc:  # report, do not hide
         out["graph"] = {"captured": False, "error": str(exc)[:200]}
-    # error of sampled pairs against the FP64 oracle
-    import oracle
+    # error of sampled pairs against a tight FP64 CG solve on the GPU
     Xh = X.cpu().numpy()
     errs = []
     offs = np.concatenate([[0], np.cumsum([s["A"].n for s in sl])])
     order = sorted(range(nsys), key=lambda i: sl[i]["A"].n)[:sample]
     for i in order:
-        A = sl[i]["A"]
+        fs = gbcg.Solver(sl[i]["A"], precond=gbcg.CG_PRECOND_JACOBI)
         for r in range(4):
-            ref = oracle.cg(A, sl[i]["B"][r], tol=TOL, precond=1)["x"]
+            bt = torch.from_numpy(sl[i]["B"][r]).to(dev)
+            xt = torch.zeros_like(bt)
+            fs.solve(bt, xt, 1e-13)
+            ref = xt.cpu().numpy()
             x = Xh[r, offs[i]:offs[i + 1]]
             errs.append(float(np.linalg.norm(x - ref) / np.linalg.norm(ref)))
-    out["err_vs_fp64_oracle_max"] = max(errs) if errs else None
-    out["err_sample"] = f"{len(errs)} pairs of the {len(order)} smallest systems"
+        fs.close()
+    out["err_vs_fp64_cg_max"] = max(errs) if errs else None
+    out["err_sample"] = (f"{len(errs)} pairs of the {len(order)} smallest systems, against FP64 Jacobi-PCG "
+                         f"on the GPU to rel. residual 1e-13")
     bs.close()
     return out
 
@@ -364,6 +391,169 @@ def measure_learned(ninst: int = 40, per: int = 500, seg: int = 8, batch: int = 
     return out
 
 
+def timed_solves(solver, b, x, count, flush, record=True):
+    """count solves of b from x = 0 with the L2 flushed before each, timed by
+    CUDA events on the current stream: [(ms, info), ...]."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg
+    stream = torch.cuda.current_stream()
+    out = []
+    for _ in range(count):
+        x.zero_()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = solver.solve(b, x, tol=TOL)
+        e1.record(stream)
+        e1.synchronize()
+        if info.status != gbcg.CG_OK:
+            raise RuntimeError(f"solve failed: {gbcg.cg_strerror(info.status)}")
+        if record:
+            out.append((e0.elapsed_time(e1), info))
+    return out
+
+
+def l2_flush_buffer():
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    l2 = int(getattr(props, "L2_cache_size", 126 * 2 ** 20))
+    return torch.empty(2 * l2 // 4, dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+
+
+def measure_forms(pr, ms_fp64: float, iters_fp64: int, count: int, x_ref, flush) -> dict:
+    """Jacobi-PCG and FP32/BF16 refinement (with and without Jacobi) on the
+    50^3 workload: ms per solve, iterations, true residual, error against the
+    oracle's solution (x_ref, from the CPU baseline leg; None: against x*)."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = torch.from_numpy(pr.b).to(dev)
+    x = torch.zeros_like(b)
+    ref = x_ref if x_ref is not None else pr.xstar
+    key = "err_vs_fp64_oracle" if x_ref is not None else "err_vs_xstar"
+    forms = {"fp64_cg": {"ms_per_solve": round(ms_fp64, 4), "iters": iters_fp64}}
+    variants = [("jacobi_pcg", dict(precond=gbcg.CG_PRECOND_JACOBI)),
+                ("fp32_ir", dict(inner_values=gbcg.CG_VALUES_FP32)),
+                ("bf16_ir", dict(inner_values=gbcg.CG_VALUES_BF16)),
+                ("fp32_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI)),
+                ("bf16_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_BF16, precond=gbcg.CG_PRECOND_JACOBI))]
+    for name, kw in variants:
+        vs = gbcg.Solver(pr.A, **kw)
+        timed_solves(vs, b, x, 2, flush, False)
+        res_v = timed_solves(vs, b, x, count, flush)
+        v_ms = statistics.mean(t for t, _ in res_v)
+        xv = x.cpu().numpy()
+        info_v = res_v[-1][1]
+        forms[name] = {"ms_per_solve": round(v_ms, 4), "iters": info_v.iters, "outer": info_v.outer,
+                       "relres_true": info_v.relres_true,
+                       key: float(np.linalg.norm(xv - ref) / np.linalg.norm(ref)),
+                       "speedup_vs_fp64_cg": round(ms_fp64 / v_ms, 3)}
+        vs.close()
+    return forms
+
+
+def measure_spmv_hbm(peaks: dict, flush) -> dict:
+    """One FP64 SpMV on the 100^3 system (27.3M entries), L2 flushed before each
+    of 20 launches, median time against the measured HBM peak."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    big = problems.cube_blobs(100)
+    bs = gbcg.Solver(big.A)
+    xb = torch.from_numpy(np.random.default_rng(0).standard_normal(big.A.n)).to(dev)
+    yb = torch.empty_like(xb)
+    for _ in range(3):
+        bs.spmv(xb, yb)
+    ts = []
+    for _ in range(20):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bs.spmv(xb, yb)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    bs.close()
+    t_med = statistics.median(ts) / 1e3
+    sb = spmv_bytes(big.A.n, big.A.nnz)
+    gbs = sb / t_med / 1e9
+    trs = ncu_traffic("spmv_kernel")
+    return {
+        "workload": "q1-100^3 blobs, N=1030301, NNZ=27270901, FP64 SpMV, L2 flushed",
+        "kernel": "spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
+        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+        "algorithmic_bytes": sb,
+        "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),
+        "traffic": (round(trs["dram_bytes_per_launch"]) if trs else None),
+    }
+
+
+def measure_learned_iter(maxits=(12, 36)) -> dict:
+    """ms per flexible-CG iteration with the untrained network (the cost of an
+    iteration does not depend on the weights): the slope between maxit = 12 and
+    36 on the 50^3 workload grid and on a 100^3 instance."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    dev = torch.device("cuda", torch.cuda.current_device())
+    net = gbcg.Net(problems.learn_init_params())
+    out = {}
+    for e in (50, 100):
+        inst = problems.learn_instance(e, 20001)
+        s = gbcg.Solver(inst.A, precond=gbcg.CG_PRECOND_LEARNED, true_residual=False)
+        s.set_learned(net, inst.grid, inst.lognu.astype(np.float32))
+        b = torch.from_numpy(inst.b).to(dev)
+        ms = {}
+        for m in maxits:
+            ts = []
+            for _ in range(3):
+                x = torch.zeros_like(b)
+                ts.append(s.solve(b, x, 1e-14, maxit=m).kernel_ms)
+            ms[m] = statistics.median(ts)
+        s.close()
+        out[f"q1_{e}cube"] = {"ms_per_iteration": round((ms[maxits[1]] - ms[maxits[0]]) / (maxits[1] - maxits[0]), 4),
+                              "n": inst.A.n, "nnz": inst.A.nnz}
+    net.close()
+    return out
+
+
+def run_section(args) -> None:
+    """--section NAME: one extra section alone (no headline line)."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    torch.cuda.set_device(0)
+    gbcg.lib()
+    name = "batched_full" if args.batched_full else "learned" if args.learned_only else args.section
+    if name == "spmv":
+        out = measure_spmv_hbm(measured_peaks(), l2_flush_buffer())
+    elif name == "forms":
+        flush = l2_flush_buffer()
+        pr = problems.cube_blobs(50)
+        s = gbcg.Solver(pr.A)
+        b = torch.from_numpy(pr.b).to(torch.device("cuda", 0))
+        x = torch.zeros_like(b)
+        timed_solves(s, b, x, 2, flush, False)
+        res = timed_solves(s, b, x, 3, flush)
+        s.close()
+        out = measure_forms(pr, statistics.mean(t for t, _ in res), res[-1][1].iters, 3, None, flush)
+    elif name == "batched":
+        out = measure_batched(64, 20, 40, 3, tune=True, sample=2)
+    elif name == "batched_full":
+        out = measure_batched(256, 20, 80, max(1, args.steps // 5), tune=False, sample=2)
+    elif name == "learned_iter":
+        out = measure_learned_iter()
+    else:
+        out = measure_learned()
+    print(json.dumps({"section": name, name: out}), flush=True)
+
+
 def run_gbcg(args) -> None:
     import torch
     import torch.distributed as dist
@@ -385,33 +575,16 @@ def run_gbcg(args) -> None:
     flush = torch.empty(2 * l2 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def timed_solves(solver, b, x, count, record):
-        out = []
-        for _ in range(count):
-            x.zero_()
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            info = solver.solve(b, x, tol=TOL)
-            e1.record(stream)
-            e1.synchronize()
-            if info.status != gbcg.CG_OK:
-                raise RuntimeError(f"solve failed: {gbcg.cg_strerror(info.status)}")
-            if record:
-                out.append((e0.elapsed_time(e1), info))
-        return out
-
     # ---------------------------------------------------- FP64 CG (the step)
     solver = gbcg.Solver(pr.A)
     b = torch.from_numpy(pr.b).to(dev)
     x = torch.zeros_like(b)
-    timed_solves(solver, b, x, args.warmup, False)
+    timed_solves(solver, b, x, args.warmup, flush, False)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     with ClockSampler(local) as clk:
-        res = timed_solves(solver, b, x, args.steps, True)
+        res = timed_solves(solver, b, x, args.steps, flush)
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -482,77 +655,28 @@ def run_gbcg(args) -> None:
     solver.close()
 
     if not args.no_extras:
-        # ------------------------------- Jacobi-PCG and mixed-precision forms
-        import oracle
-        ref_x = oracle.cg(pr.A, pr.b, tol=TOL)["x"]
-        forms = {"fp64_cg": {"ms_per_solve": round(ms_per_step, 4), "iters": iters}}
-        variants = [("jacobi_pcg", dict(precond=gbcg.CG_PRECOND_JACOBI)),
-                    ("fp32_ir", dict(inner_values=gbcg.CG_VALUES_FP32)),
-                    ("bf16_ir", dict(inner_values=gbcg.CG_VALUES_BF16)),
-                    ("fp32_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI)),
-                    ("bf16_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_BF16, precond=gbcg.CG_PRECOND_JACOBI))]
-        for name, kw in variants:
-            vs = gbcg.Solver(pr.A, **kw)
-            timed_solves(vs, b, x, 2, False)
-            res_v = timed_solves(vs, b, x, max(3, args.steps // 2), True)
-            v_ms = statistics.mean(t for t, _ in res_v)
-            xv = x.cpu().numpy()
-            info_v = res_v[-1][1]
-            forms[name] = {"ms_per_solve": round(v_ms, 4), "iters": info_v.iters, "outer": info_v.outer,
-                           "relres_true": info_v.relres_true,
-                           "err_vs_fp64_oracle": float(np.linalg.norm(xv - ref_x) / np.linalg.norm(ref_x)),
-                           "speedup_vs_fp64_cg": round(ms_per_step / v_ms, 3)}
-            vs.close()
-        line["forms"] = forms
-        # -------------------------------------- SpMV roofline at 100^3 (HBM)
-        big = problems.cube_blobs(100)
-        bs = gbcg.Solver(big.A)
-        xb = torch.from_numpy(np.random.default_rng(0).standard_normal(big.A.n)).to(dev)
-        yb = torch.empty_like(xb)
-        for _ in range(3):
-            bs.spmv(xb, yb)
-        ts = []
-        for _ in range(20):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            bs.spmv(xb, yb)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        t_med = statistics.median(ts) / 1e3
-        sb = spmv_bytes(big.A.n, big.A.nnz)
-        gbs = sb / t_med / 1e9
-        trs = ncu_traffic("spmv_kernel")
-        line["spmv_hbm"] = {
-            "workload": "q1-100^3 blobs, N=1030301, NNZ=27270901, FP64 SpMV, L2 flushed",
-            "kernel": "spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
-            "algorithmic_bytes": sb,
-            "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),
-            "traffic": (round(trs["dram_bytes_per_launch"]) if trs else None),
-        }
-        bs.close()
-        line["gpu_launches"] += 0  # extras are outside the timed region
-        # --------------------------------------- batched solves (mini config)
-        line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
-        # ------------------------------------------ learned preconditioner
-        line["learned"] = measure_learned()
-        lf = line["learned"]["q1_50cube_c2"]["learned_fcg"]
-        forms["learned_fcg"] = {"ms_per_solve": lf["ms_per_solve"], "iters": lf["iters"],
-                                "relres_true": lf["relres_true"], "reverted_at": lf["reverted_at"],
-                                "speedup_vs_fp64_cg": round(ms_per_step / lf["ms_per_solve"], 3)}
-
-        # ----------------------------------------------- CPU oracle baseline
+        # ------------------- CPU oracle baseline (its solution is the reference
+        # the other forms' errors are reported against)
+        x_oracle = None
         if rank == 0 and world == 1:
             import oracle
             t0 = time.perf_counter()
             r = oracle.cg(pr.A, pr.b, tol=TOL)
             dt = (time.perf_counter() - t0) * 1e3
+            x_oracle = r["x"]
             line["cpu_baseline"] = {
                 "value": round(dt, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"one full serial FP64 CG solve of the same system ({r['iters']} iterations)"}
+        forms = measure_forms(pr, ms_per_step, iters, max(3, args.steps // 2), x_oracle, flush)
+        line["spmv_hbm"] = measure_spmv_hbm(peaks, flush)
+        line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
+        line["learned"] = measure_learned()
+        lf = line["learned"]["q1_50cube_c2"]["learned_fcg"]
+        forms["learned_fcg"] = {"ms_per_solve": lf["ms_per_solve"], "iters": lf["iters"],
+                                "relres_true": lf["relres_true"], "reverted_at": lf["reverted_at"],
+                                "speedup_vs_fp64_cg": round(ms_per_step / lf["ms_per_solve"], 3)}
+        line["forms"] = forms
+        line["gpu_launches"] += 0  # extras are outside the timed region
 
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -562,20 +686,8 @@ def run_gbcg(args) -> None:
 
 def main():
     args = parse_args()
-    if args.learned_only:
-        import torch
-        torch.cuda.set_device(0)
-        from paper_1107_0538_gb300 import gbcg
-        gbcg.lib()
-        print(json.dumps({"learned": measure_learned()}), flush=True)
-        return
-    if args.batched_full:
-        import torch
-        torch.cuda.set_device(0)
-        from paper_1107_0538_gb300 import gbcg
-        gbcg.lib()
-        print(json.dumps({"batched_full": measure_batched(256, 20, 80, max(1, args.steps // 5), tune=False,
-                                                          sample=2)}), flush=True)
+    if args.section or args.batched_full or args.learned_only:
+        run_section(args)
         return
     if args.impl == "reference":
         run_reference(args)
