@@ -88,7 +88,7 @@ def measured_peaks() -> dict:
 _COMMON = ["cg_device.cuh", "layout.h"]
 KERNEL_SOURCES = {
     "cg_solve_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
-    "spmv_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
+    "sell_spmv_kernel": ["gbcg.cu", "sell.cuh", "plan.h"],
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
     "conv16_kernel": ["learn.cu"] + _COMMON,
@@ -456,8 +456,9 @@ def measure_forms(pr, ms_fp64: float, iters_fp64: int, count: int, x_ref, flush)
 
 
 def measure_spmv_hbm(peaks: dict, flush) -> dict:
-    """One FP64 SpMV on the 100^3 system (27.3M entries), L2 flushed before each
-    of 20 launches, median time against the measured HBM peak."""
+    """One FP64 SpMV (cg_spmv: the SELL-32 kernel) on the 100^3 system (27.3M
+    entries), L2 flushed before each of 20 launches, median time against the
+    measured HBM peak."""
     import torch
 
     from paper_1107_0538_gb300 import gbcg, problems
@@ -483,10 +484,10 @@ def measure_spmv_hbm(peaks: dict, flush) -> dict:
     t_med = statistics.median(ts) / 1e3
     sb = spmv_bytes(big.A.n, big.A.nnz)
     gbs = sb / t_med / 1e9
-    trs = ncu_traffic("spmv_kernel")
+    trs = ncu_traffic("sell_spmv_kernel")
     return {
         "workload": "q1-100^3 blobs, N=1030301, NNZ=27270901, FP64 SpMV, L2 flushed",
-        "kernel": "spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
+        "kernel": "sell_spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
         "algorithmic_bytes": sb,
         "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),

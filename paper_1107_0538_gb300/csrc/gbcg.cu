@@ -574,15 +574,10 @@ out:
     drain<float, float>(P, S, pipe, P.p32);
 }
 
-// ------------------------------------------------------- plain SpMV kernel
-__global__ void __launch_bounds__(kThreads, 1) spmv_kernel(Params P) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Smem S = carve_smem(smem_raw);
-    init_pipeline(S);
-    Pipe pipe;
-    EpiStore epi{P.q};
-    (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, epi, true);
-    drain<double, double>(P, S, pipe, P.x);
+// y = A x in the SELL-32 layout (stand-alone SpMV).
+__global__ void __launch_bounds__(kSellThreads) sell_spmv_kernel(SellMatrix M, const double *x, double *y) {
+    EpiStore epi{y};
+    sell_rows(M, x, epi);
 }
 
 constexpr int kRptChoices[] = {0, 1, 2, 4};
@@ -729,10 +724,7 @@ int gbcg::enqueue_fp64_solve(cg_handle *h, const double *b, double *x, double to
 }
 
 int gbcg::enqueue_spmv(cg_handle *h, const double *x, double *y) {
-    Params P = base_params(h);
-    P.x = const_cast<double *>(x);
-    P.q = y;
-    spmv_kernel<<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P);
+    sell_spmv_kernel<<<h->sell_grid, kSellThreads, 0, h->stream>>>(sell_of(h), x, y);
     return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
 }
 
@@ -869,8 +861,8 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
             return fail(CG_ECUDA);
     }
-    if (cudaFuncSetAttribute((const void *)spmv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBytes) != cudaSuccess ||
+    if (cudaFuncSetAttribute((const void *)sell_spmv_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxL1) != cudaSuccess ||
         cudaFuncSetAttribute((const void *)cg_ir_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmemBytes) != cudaSuccess ||
         cudaFuncSetAttribute((const void *)cg_ir_kernel<__nv_bfloat16>,
@@ -955,6 +947,25 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         } else {
             h->z32 = h->r32;
         }
+    }
+    {   // SELL-32 copy for the stand-alone SpMV
+        const SellHost sh = build_sell(n, rowptr, colidx, vals);
+        h->sell_slices = (n + 31) / 32;
+        h->sell_grid = std::max(1, std::min(sms * kSellBlocksPerSm, (h->sell_slices + 7) / 8));
+        const size_t tot = sh.vals.size();
+        if ((rc = dev_alloc(h, &h->sell_ptr, sh.ptr.size())) || (rc = dev_alloc(h, &h->sell_vals, tot)))
+            return fail(rc);
+        if (sh.rel16) rc = dev_alloc(h, &h->sell_c16, tot);
+        else rc = dev_alloc(h, &h->sell_c32, tot);
+        if (rc) return fail(rc);
+        cudaError_t es = cudaMemcpy(h->sell_ptr, sh.ptr.data(), sizeof(long long) * sh.ptr.size(),
+                                    cudaMemcpyHostToDevice);
+        if (es == cudaSuccess && tot)
+            es = cudaMemcpy(h->sell_vals, sh.vals.data(), sizeof(double) * tot, cudaMemcpyHostToDevice);
+        if (es == cudaSuccess && tot)
+            es = sh.rel16 ? cudaMemcpy(h->sell_c16, sh.cols16.data(), 2 * tot, cudaMemcpyHostToDevice)
+                          : cudaMemcpy(h->sell_c32, sh.cols32.data(), 4 * tot, cudaMemcpyHostToDevice);
+        if (es != cudaSuccess) return fail(cuda_fail(es));
     }
     if (cudaMallocHost(&h->st_host, sizeof(DevStatus)) != cudaSuccess) return fail(CG_ENOMEM);
     if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
@@ -1060,18 +1071,7 @@ int cg_spmv(cg_handle *h, const double *x, double *y) {
     if (h->n == 0) return CG_OK;
     if (!x || !y || x == y) return CG_EINVAL;
     DeviceGuard g(h->device);
-    Params P = base_params(h);
-    P.x = const_cast<double *>(x);
-    if (reinterpret_cast<uintptr_t>(x) % 16 != 0) {
-        // x-windows are TMA copies and need a 16-byte aligned source
-        if (cudaMemcpyAsync(h->x_dev, x, sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToDevice,
-                            h->stream) != cudaSuccess)
-            return CG_ECUDA;
-        P.x = h->x_dev;
-    }
-    P.q = y;
-    spmv_kernel<<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P);
-    return cudaGetLastError() == cudaSuccess ? CG_OK : CG_ECUDA;
+    return enqueue_spmv(h, x, y);
 }
 
 int cg_get_plan(const cg_handle *h, cg_plan *plan) {

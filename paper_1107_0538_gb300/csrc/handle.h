@@ -10,6 +10,7 @@
 
 #include "cg_device.cuh"
 #include "gbcg.h"
+#include "sell.cuh"
 
 namespace gbcg {
 using SolveKernel = void (*)(Params);
@@ -47,6 +48,13 @@ struct cg_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<void *> allocs;
     gbcg::LearnCtx *learn = nullptr;  // set by cg_set_learned
+    // SELL-32 copy of the matrix (stand-alone and flexible-CG SpMV)
+    long long *sell_ptr = nullptr;
+    double *sell_vals = nullptr;
+    int16_t *sell_c16 = nullptr;
+    int32_t *sell_c32 = nullptr;
+    int32_t sell_slices = 0;
+    int sell_grid = 0;                // CTAs of a SELL SpMV launch
 };
 
 namespace gbcg {
@@ -80,10 +88,14 @@ struct DeviceGuard {
 
 // Kernel parameters of the handle's matrix, tiles and workspace (gbcg.cu).
 Params base_params(const cg_handle *h);
+// The handle's SELL-32 matrix.
+inline SellMatrix sell_of(const cg_handle *h) {
+    return SellMatrix{h->n, h->sell_slices, h->evict_first, h->sell_ptr, h->sell_vals, h->sell_c16, h->sell_c32};
+}
 // Enqueues one persistent FP64 CG solve with the given preconditioner flag
 // (0 plain, 1 Jacobi) on the handle's stream, without synchronizing (gbcg.cu).
 int enqueue_fp64_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, int precond);
-// Enqueues y = A x with the tiled SpMV; x 16-byte aligned (gbcg.cu).
+// Enqueues y = A x (SELL-32 SpMV) on the handle's stream (gbcg.cu).
 int enqueue_spmv(cg_handle *h, const double *x, double *y);
 // Flexible CG with the learned preconditioner (learn.cu).
 int learn_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info);

@@ -781,14 +781,9 @@ __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgStat
 }
 
 // Plain y = A x for training (no reductions).
-__global__ void __launch_bounds__(kThreads, 1) spmv_store_kernel(Params P, const double *x, double *y) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const Smem S = carve_smem(smem_raw);
-    init_pipeline(S);
-    Pipe pipe;
+__global__ void __launch_bounds__(kSellThreads) spmv_store_kernel(SellMatrix M, const double *x, double *y) {
     EpiStoreY e{y};
-    (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, x, e, true);
-    drain<double, double>(P, S, pipe, x);
+    sell_rows(M, x, e);
 }
 
 // ------------------------------------------------------------ training
@@ -1209,18 +1204,19 @@ int set_smem_limits() {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return CG_ECUDA;
     cudaError_t e = cudaSuccess;
-    // every kernel of a solve asks for the same (maximal) shared-memory
-    // carveout, so that consecutive kernels never wait for the SMs to be
-    // reconfigured
     auto set = [&](const void *f) {
         cudaFuncAttributes fa{};
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      optin - (int)fa.sharedSizeBytes);
+    };
+    // the SELL SpMVs stage nothing: all of the SM's storage goes to L1, where
+    // the gathers of x find the neighbours other warps already loaded
+    auto l1 = [&](const void *f) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared);
+                                     (int)cudaSharedmemCarveoutMaxL1);
     };
     set((const void *)conv16_kernel<E_STORE>);
     set((const void *)conv16_kernel<E_GATE>);
@@ -1234,13 +1230,12 @@ int set_smem_limits() {
     set((const void *)fcg_spmv_kernel<S_SETUP>);
     set((const void *)fcg_spmv_kernel<S_Q>);
     set((const void *)fcg_spmv_kernel<S_TRUE>);
-    set((const void *)spmv_store_kernel);
+    l1((const void *)spmv_store_kernel);
     set((const void *)conv1_kernel<E_GATE>);
     set((const void *)conv1_kernel<E_SIGMOID>);
     set((const void *)conv1_kernel<E_GATE_PRE>);
     set((const void *)conv1_kernel<E_BWD_GATE>);
-    set((const void *)fcg_p_kernel);
-    set((const void *)fcg_xr_kernel);
+
     if (e != cudaSuccess) return CG_ECUDA;
     done = 1;
     return CG_OK;
@@ -1321,8 +1316,7 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
     const VecArgs V = vec_args(h, L);
     fcg_p_kernel<<<L->vgrid, kVT, 0, s>>>(V);
-    Params P = learn_params(h, L);
-    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, L->p, L->partials, V);
+    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, L->p, L->partials, V);
     fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
 }
 
@@ -1455,9 +1449,7 @@ void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
     convout_kernel<E_OUT_U><<<G.tiles, kCT, convout_smem(G), s>>>(A);
     // loss: v = u - e_hat, w = A_hat v
     loss_prep_kernel<<<vg, kVT, 0, s>>>(T);
-    Params P = base_params(h);
-    P.st = L->dst;
-    spmv_store_kernel<<<h->ctas, kThreads, kSmemBytes, s>>>(P, net->t, net->y);
+    spmv_store_kernel<<<h->sell_grid, kSellThreads, 0, s>>>(sell_of(h), net->t, net->y);
     loss_kernel<<<vg, kVT, 0, s>>>(T);
     // backward
     WgArgs W{};
@@ -1579,9 +1571,8 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
     if (e != cudaSuccess) return CG_ECUDA;
     int launches = 0;
     launch_gates(L, net, s);
-    Params P = learn_params(h, L);
-    fcg_spmv_kernel<S_SETUP><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials,
-                                                                   vec_args(h, L));
+    fcg_spmv_kernel<S_SETUP><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, h->x_dev,
+                                                                   L->partials, vec_args(h, L));
     launches += 2;
     if (cudaGetLastError() != cudaSuccess) return CG_ECUDA;
     // graph launches, two in flight; each body advances the iteration count
@@ -1611,8 +1602,8 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
     if (h->opts.true_residual) {
-        fcg_spmv_kernel<S_TRUE><<<h->ctas, kThreads, kSmemBytes, s>>>(P, L->st, h->x_dev, L->partials,
-                                                                      vec_args(h, L));
+        fcg_spmv_kernel<S_TRUE><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, h->x_dev,
+                                                                      L->partials, vec_args(h, L));
         ++launches;
     }
     e = cudaEventRecord(L->t1, s);
@@ -1748,7 +1739,7 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
     L->vgrid = std::min((G.n + kVT - 1) / kVT, 4 * sms);
     const size_t a16 = act_count(G, kCh);
     auto &A = L->allocs;
-    const int nparts = std::max({L->vgrid, G.tiles, h->ctas});
+    const int nparts = std::max({L->vgrid, G.tiles, h->ctas, h->sell_grid});
     if ((rc = ctx_alloc(A, &L->lognu_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->gates, a16)) ||
         (rc = ctx_alloc(A, &L->s_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->pidx, (size_t)G.n)) ||
         (rc = ctx_alloc(A, &L->h1, a16)) || (rc = ctx_alloc(A, &L->h2, a16)) || (rc = ctx_alloc(A, &L->k1, a16)) ||

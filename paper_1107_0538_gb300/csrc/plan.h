@@ -337,4 +337,58 @@ inline std::string check_plan(int32_t n, const std::vector<int32_t> &rowptr,
     return std::string();
 }
 
+// SELL-32 copy of a CSR matrix (see sell.cuh): slices of 32 rows padded to
+// their longest row, entries k-major within a slice; 16-bit column offsets
+// from the row when all fit, else 32-bit columns.
+struct SellHost {
+    std::vector<long long> ptr;
+    std::vector<double> vals;
+    std::vector<int16_t> cols16;
+    std::vector<int32_t> cols32;
+    bool rel16 = true;
+};
+
+inline SellHost build_sell(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
+                           const std::vector<double> &vals) {
+    SellHost S;
+    const int ns = (n + 31) / 32;
+    S.ptr.assign((size_t)ns + 1, 0);
+    for (int t = 0; t < ns; ++t) {
+        int w = 0;
+        for (int r = t * 32; r < std::min(n, t * 32 + 32); ++r) w = std::max(w, rowptr[r + 1] - rowptr[r]);
+        S.ptr[t + 1] = S.ptr[t] + 32LL * w;
+    }
+    const size_t tot = (size_t)S.ptr[ns];
+    for (int32_t r = 0; r < n && S.rel16; ++r)
+        for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            const int rel = colidx[k] - r;
+            if (rel < -32768 || rel > 32767) {
+                S.rel16 = false;
+                break;
+            }
+        }
+    S.vals.assign(tot, 0.0);
+    if (S.rel16) S.cols16.assign(tot, 0);
+    else S.cols32.assign(tot, 0);
+    for (int t = 0; t < ns; ++t) {
+        const int w = (int)((S.ptr[t + 1] - S.ptr[t]) / 32);
+        for (int l = 0; l < 32; ++l) {
+            const int r = t * 32 + l;
+            for (int k = 0; k < w; ++k) {
+                const size_t idx = (size_t)S.ptr[t] + (size_t)k * 32 + l;
+                int col = r < n ? r : n - 1;   // padding: value 0 at an in-range column
+                double v = 0.0;
+                if (r < n && k < rowptr[r + 1] - rowptr[r]) {
+                    col = colidx[rowptr[r] + k];
+                    v = vals[rowptr[r] + k];
+                }
+                S.vals[idx] = v;
+                if (S.rel16) S.cols16[idx] = (int16_t)(col - r);
+                else S.cols32[idx] = col;
+            }
+        }
+    }
+    return S;
+}
+
 }  // namespace gbcg

@@ -1,7 +1,9 @@
 // CPU driver for the host tile planner (paper_1107_0538_gb300/csrc/plan.h):
 // reads a CSR pattern (n, nnz, rowptr, colidx as raw int32 little-endian
 // from a file), plans tiles and x-windows exactly as cg_create does, runs
-// check_plan on the result and prints a one-line JSON summary.
+// check_plan on the result, builds the SELL-32 copy and checks that every
+// stored entry decodes back to its CSR entry and every padded entry is a
+// zero at an in-range column; prints a one-line JSON summary.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -32,8 +34,42 @@ int main(int argc, char **argv) {
             maxwin = std::max(maxwin, d1.z);
         }
     }
+    // SELL-32: values are the entry numbers + 1, so each decodes uniquely
+    std::vector<double> vals(nnz);
+    for (int32_t k = 0; k < nnz; ++k) vals[k] = k + 1.0;
+    const gbcg::SellHost sh = gbcg::build_sell(n, rowptr, colidx, vals);
+    std::string sell_err;
+    const int ns = (n + 31) / 32;
+    if ((int)sh.ptr.size() != ns + 1 || sh.ptr[0] != 0) sell_err = "slice pointers";
+    for (int t = 0; t < ns && sell_err.empty(); ++t) {
+        const long long span = sh.ptr[t + 1] - sh.ptr[t];
+        int w = 0;
+        for (int r = t * 32; r < std::min(n, t * 32 + 32); ++r) w = std::max(w, rowptr[r + 1] - rowptr[r]);
+        if (span != 32LL * w) sell_err = "slice width";
+        for (int l = 0; l < 32 && sell_err.empty(); ++l) {
+            const int r = t * 32 + l;
+            for (int k = 0; k < w; ++k) {
+                const size_t idx = (size_t)sh.ptr[t] + (size_t)k * 32 + l;
+                const int col = sh.rel16 ? r + sh.cols16[idx] : sh.cols32[idx];
+                const bool real = r < n && k < rowptr[r + 1] - rowptr[r];
+                if (col < 0 || col >= n) { sell_err = "column out of range"; break; }
+                if (real && (col != colidx[rowptr[r] + k] || sh.vals[idx] != vals[rowptr[r] + k])) {
+                    sell_err = "entry does not decode";
+                    break;
+                }
+                if (!real && sh.vals[idx] != 0.0) { sell_err = "nonzero padding"; break; }
+            }
+        }
+    }
+    bool fits = true;
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k)
+            if (colidx[k] - r < -32768 || colidx[k] - r > 32767) fits = false;
+    if (sell_err.empty() && fits != sh.rel16) sell_err = "wrong column width";
     std::printf("{\"tiles\": %d, \"windowed\": %d, \"long\": %d, \"max_tile_nnz\": %d, "
-                "\"max_segments\": %d, \"max_window_tx\": %d, \"error\": \"%s\"}\n",
-                nt, tp.windowed, longs, max_nnz, maxseg, maxwin, problem.c_str());
-    return problem.empty() ? 0 : 1;
+                "\"max_segments\": %d, \"max_window_tx\": %d, \"sell_entries\": %lld, \"sell_rel16\": %d, "
+                "\"error\": \"%s%s\"}\n",
+                nt, tp.windowed, longs, max_nnz, maxseg, maxwin, (long long)sh.ptr.back(), (int)sh.rel16,
+                problem.c_str(), sell_err.c_str());
+    return problem.empty() && sell_err.empty() ? 0 : 1;
 }

@@ -93,3 +93,15 @@ def test_banded_windows_with_odd_tail(checker):
 def test_empty_matrix(checker):
     run_plan(checker, [0], [], 0)
     run_plan(checker, [0] * 51, [], 50)
+
+
+def test_sell_column_widths(checker):
+    # 16-bit column offsets when every |col - row| < 2^15, else 32-bit columns
+    e = 20
+    A = problems.q1_matrix(problems.nu_uniform(e, e, e), 1.0 / e)[0]
+    out = run_plan(checker, A.rowptr, A.colidx, A.n)
+    assert out["sell_rel16"] == 1
+    assert out["sell_entries"] >= A.nnz and out["sell_entries"] % 32 == 0
+    rowptr, cols = random_pattern(70000, 8)   # random columns reach past 2^15
+    out = run_plan(checker, rowptr, cols, 70000)
+    assert out["sell_rel16"] == 0
