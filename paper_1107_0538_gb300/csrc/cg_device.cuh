@@ -53,7 +53,8 @@ struct Params {
     double *x;
     double *r;
     double *z;          // == r for plain CG
-    double *p0;         // search direction p
+    double *p0;         // vector the SpMV gathers (padded, 16-byte aligned): z (FP64 CG), p (IR inner)
+    double *pd;         // search direction p of the FP64 CG in memory mode (own rows)
     double *q;
     double *partials;   // 2 sets x gridDim.x x kRedSlots
     unsigned int *bar;  // grid barrier counter (zeroed before each launch)

@@ -9,12 +9,16 @@
 // per SM) bounds this path before HBM does, so every phase does exactly the
 // FP64 operations of the recurrence and nothing more:
 //
-//   phase A  q = A p over this CTA's rows (matrix streamed by TMA per warp),
+//   phase A  p = z + beta p and q = A z + beta q over this CTA's rows (the
+//            SpMV gathers z, streamed by TMA per warp; A p = A z + beta A p_old),
 //            partial p.q                                  -> grid barrier
-//   phase B  x += alpha p, r -= alpha q, z = dinv r, partial r.r and r.z
-//                                                         -> grid barrier
+//   phase B  x += alpha p, r -= alpha q, z = dinv r (published for the
+//            next SpMV), partial r.r and r.z              -> grid barrier
 //            every CTA takes the same stop decision
-//   phase C  p = z + beta p                               -> grid barrier
+//
+// Two grid barriers per iteration: the direction p is only ever needed on
+// the rows a thread owns, so it is updated inside phase A instead of in a
+// phase of its own.
 //
 // Scalars never leave the device; sums are fixed-order (bitwise
 // reproducible from run to run).
@@ -54,11 +58,13 @@ struct RegRows {
 };
 
 // ------------------------------------------------------------ epilogues
-struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
+struct EpiSetup {       // r = b - A x0, z = M^-1 r (gathered), p = z, q = 0; sums r.r, r.z, b.b
     const double *b;
     double *r;
     double *z;
-    double *p;
+    double *p;          // gathered copy of z
+    double *pd;         // direction
+    double *q;
     const double *dinv;
     int precond;
     double rr = 0.0, rz = 0.0, bb = 0.0;
@@ -72,6 +78,8 @@ struct EpiSetup {       // r = b - A x0, z = M^-1 r, p = z; sums r.r, r.z, b.b
             z[i] = zi;
         }
         p[i] = zi;
+        pd[i] = zi;
+        q[i] = 0.0;
         rr = fma(ri, ri, rr);
         rz = fma(ri, zi, rz);
         bb = fma(bi, bi, bb);
@@ -92,6 +100,7 @@ struct RegSetup {       // the same, into registers (p is also published)
         R.r[j] = ri;
         R.z[j] = zi;
         R.p[j] = zi;
+        R.q[j] = 0.0;
         p[i] = zi;
         rr = fma(ri, ri, rr);
         rz = fma(ri, zi, rz);
@@ -99,23 +108,32 @@ struct RegSetup {       // the same, into registers (p is also published)
     }
 };
 
-struct EpiIter {        // q = A p; sum p . q
+struct EpiIter {        // p = z + beta p, q = A z + beta q; sum p . q
     double *q;
-    const double *p;
+    double *pd;
+    const double *z;    // the gathered vector (own rows read back)
+    double beta;
     double pq = 0.0;
-    __device__ __forceinline__ void row(int i, double aq, int) {
-        q[i] = aq;
-        pq = fma(p[i], aq, pq);
+    __device__ __forceinline__ void row(int i, double az, int) {
+        const double qi = fma(beta, q[i], az);
+        const double pi = fma(beta, pd[i], z[i]);
+        q[i] = qi;
+        pd[i] = pi;
+        pq = fma(pi, qi, pq);
     }
 };
 
 template <int RPT>
 struct RegIter {
     RegRows<RPT> &R;
+    double beta;
     double pq = 0.0;
-    __device__ __forceinline__ void row(int, double aq, int j) {
-        R.q[j] = aq;
-        pq = fma(R.p[j], aq, pq);
+    __device__ __forceinline__ void row(int, double az, int j) {
+        const double qi = fma(beta, R.q[j], az);
+        const double pi = fma(beta, R.p[j], R.z[j]);
+        R.q[j] = qi;
+        R.p[j] = pi;
+        pq = fma(pi, qi, pq);
     }
 };
 
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
             if (!spmv_tiles<RPT, double, double, double>(P, S, pipe, P.vals, P.x, epi)) goto out;
             v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
         } else {
-            EpiSetup epi{P.b, P.r, P.z, p, P.dinv, P.precond};
+            EpiSetup epi{P.b, P.r, P.z, p, P.pd, P.q, P.dinv, P.precond};
             if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, epi)) goto out;
             v[0] = epi.rr; v[1] = epi.rz; v[2] = epi.bb;
         }
@@ -239,15 +257,16 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
     // ---- the CG loop
     if (run) {
         if (tid == 0) status = CG_ENOCONV;
+        double beta = 0.0;  // p_1 = z_0 and q_1 = A z_0
         for (int k = 1; k <= P.maxit; ++k) {
-            // phase A: q = A p, p . q
+            // phase A: p = z + beta p, q = A z + beta q (= A p), p . q
             double pq;
             if constexpr (RPT > 0) {
-                RegIter<RPT> ei{R};
+                RegIter<RPT> ei{R, beta};
                 if (!spmv_tiles<RPT, double, double, double>(P, S, pipe, P.vals, p, ei)) goto out;
                 pq = ei.pq;
             } else {
-                EpiIter ei{P.q, p};
+                EpiIter ei{P.q, P.pd, p, beta};
                 if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, p, ei)) goto out;
                 pq = ei.pq;
             }
@@ -271,7 +290,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
             if (!S.ctl[kCtlRun]) break;
             const double alpha = S.bcast[0];
 
-            // phase B: x += alpha p, r -= alpha q, z = dinv r; r.r, r.z
+            // phase B: x += alpha p, r -= alpha q, z = dinv r (published for
+            // the next SpMV: every gather of phase A is over); r.r, r.z
             double prr = 0.0, prz = 0.0;
             if constexpr (RPT > 0) {
 #pragma unroll
@@ -281,27 +301,28 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
                         const double ri = fma(-alpha, R.q[j], R.r[j]);
                         R.r[j] = ri;
                         prr = fma(ri, ri, prr);
+                        double zi = ri;
                         if (P.precond) {
-                            const double zi = R.dinv[j] * ri;
-                            R.z[j] = zi;
+                            zi = R.dinv[j] * ri;
                             prz = fma(ri, zi, prz);
-                        } else {
-                            R.z[j] = ri;
                         }
+                        R.z[j] = zi;
+                        p[R.row[j]] = zi;
                     }
                 }
             } else {
                 for (int i = row_lo + tid; i < row_hi; i += kThreads) {
-                    const double pi = p[i], qi = P.q[i], xi = P.x[i], ri0 = P.r[i];
+                    const double pi = P.pd[i], qi = P.q[i], xi = P.x[i], ri0 = P.r[i];
                     P.x[i] = fma(alpha, pi, xi);
                     const double ri = fma(-alpha, qi, ri0);
                     P.r[i] = ri;
                     prr = fma(ri, ri, prr);
+                    double zi = ri;
                     if (P.precond) {
-                        const double zi = P.dinv[i] * ri;
-                        P.z[i] = zi;
+                        zi = P.dinv[i] * ri;
                         prz = fma(ri, zi, prz);
                     }
+                    p[i] = zi;
                 }
             }
             double t2[2];
@@ -340,21 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_solve_kernel(Params P) {
             }
             __syncthreads();
             if (!S.ctl[kCtlRun]) break;
-            const double beta = S.bcast[1];
-
-            // phase C: p = z + beta p
-            if constexpr (RPT > 0) {
-#pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    if (R.row[j] >= 0) {
-                        R.p[j] = fma(beta, R.p[j], R.z[j]);
-                        p[R.row[j]] = R.p[j];
-                    }
-                }
-            } else {
-                for (int i = row_lo + tid; i < row_hi; i += kThreads) p[i] = fma(beta, p[i], P.z[i]);
-            }
-            if (!grid_barrier(P, epoch, S)) goto out;
+            beta = S.bcast[1];
         }
     }
 
@@ -640,6 +647,7 @@ Params gbcg::base_params(const cg_handle *h) {
     P.r = h->r;
     P.z = h->z;
     P.p0 = h->p0;
+    P.pd = h->pd;
     P.q = h->q;
     P.partials = h->partials;
     P.bar = h->bar;
@@ -914,6 +922,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         (rc = dev_alloc(h, &h->r, (size_t)n)) ||
         (rc = dev_alloc(h, &h->p0, (size_t)n + pad)) ||
         (rc = dev_alloc(h, &h->q, (size_t)n)) ||
+        (rc = dev_alloc(h, &h->pd, (size_t)n)) ||
         (rc = dev_alloc(h, &h->b_dev, (size_t)n)) ||
         (rc = dev_alloc(h, &h->x_dev, (size_t)n + pad)) ||
         (rc = dev_alloc(h, &h->partials, (size_t)2 * ctas * kRedSlots)) ||

@@ -41,6 +41,7 @@ struct cg_handle {
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
     double *vals = nullptr, *dinv = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
+    double *pd = nullptr;             // direction of the FP64 CG in memory mode
     double *partials = nullptr, *b_dev = nullptr, *x_dev = nullptr;
     unsigned int *bar = nullptr;
     gbcg::DevStatus *st = nullptr;
