@@ -36,7 +36,8 @@ struct Params {
     const float *__restrict__ dinv32;     // 1 / diag_lo (inner Jacobi)
     float *r32;         // inner residual
     float *z32;         // inner preconditioned residual (== r32 without Jacobi)
-    float *p32;         // inner direction (padded, 16-byte aligned: window source)
+    float *p32;         // vector the inner SpMV gathers: z (padded, 16-byte aligned: window source)
+    float *pd32;        // inner direction p
     float *q32;         // A_lo p
     float *d32;         // inner correction
     double inner_tol;

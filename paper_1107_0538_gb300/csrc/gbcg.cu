@@ -410,9 +410,10 @@ out:
 // and per-thread sums) on the low-precision copy of A (FP32 or BF16
 // off-diagonals plus the compensated FP32 diagonal), optionally with Jacobi,
 // until its residual falls by inner_tol.  One persistent launch runs it all.
-struct EpiOuter {       // r = b - A x; inner start r32 = z32/p32, d32 = 0
+struct EpiOuter {       // r = b - A x; inner start: r32, z32 = M r32 (gathered copy in p32),
+                        // direction pd32 = z32, q32 = 0, d32 = 0
     const double *b;
-    float *r32, *z32, *p32, *d32;
+    float *r32, *p32, *pd32, *q32, *d32;
     const float *dinv32;
     int precond;
     double rr = 0.0, bb = 0.0;
@@ -425,22 +426,27 @@ struct EpiOuter {       // r = b - A x; inner start r32 = z32/p32, d32 = 0
         const float rf = (float)ri;
         r32[i] = rf;
         const float zf = precond ? dinv32[i] * rf : rf;
-        if (precond) z32[i] = zf;
         p32[i] = zf;
+        pd32[i] = zf;
+        q32[i] = 0.0f;
         d32[i] = 0.0f;
         rz = fmaf(rf, zf, rz);
     }
 };
 
-struct EpiInner {       // q = A_lo p (+ compensated diagonal); sum p . q
+struct EpiInner {       // p = z + beta p, q = A_lo z + beta q (A_lo with its compensated diagonal); p . q
     float *q32;
-    const float *p32;
+    float *pd32;
+    const float *z32;   // the gathered vector (own rows read back)
     const float *diag;
+    float beta;
     float pq = 0.0f;
     __device__ __forceinline__ void row(int i, float s, int) {
-        const float pi = p32[i];
-        const float qi = fmaf(diag[i], pi, s);
+        const float zi = z32[i];
+        const float qi = fmaf(beta, q32[i], fmaf(diag[i], zi, s));
+        const float pi = fmaf(beta, pd32[i], zi);
         q32[i] = qi;
+        pd32[i] = pi;
         pq = fmaf(pi, qi, pq);
     }
 };
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
         // ---- outer residual in FP64 and the start of the inner solve
         double rho;
         {
-            EpiOuter eo{P.b, P.r32, P.z32, P.p32, P.d32, P.dinv32, P.precond};
+            EpiOuter eo{P.b, P.r32, P.p32, P.pd32, P.q32, P.d32, P.dinv32, P.precond};
             if (!spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, P.x, eo, true)) goto out;
             double v[3] = {eo.rr, eo.bb, (double)eo.rz};
             block_sum<3>(v, S);
@@ -502,9 +508,11 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
             rho = S.bcast[0];  // only thread 0 uses rho; the others never read it again
         }
 
-        // ---- inner CG in FP32 on A_lo d = r
+        // ---- inner CG in FP32 on A_lo d = r (two barriers per iteration, as
+        // in the FP64 solve: the SpMV gathers z and q = A z + beta q)
+        float beta = 0.0f;
         for (int k = 1;; ++k) {
-            EpiInner ei{P.q32, P.p32, P.diag_lo};
+            EpiInner ei{P.q32, P.pd32, P.p32, P.diag_lo, beta};
             if (!spmv_tiles<0, VT, float, float>(P, S, pipe, vlo, P.p32, ei, true)) goto out;
             double v1[1] = {(double)ei.pq};
             block_sum<1>(v1, S);
@@ -525,15 +533,16 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
             const float alpha = (float)S.bcast[2];
             float prr = 0.0f, prz = 0.0f;
             for (int i = row_lo + tid; i < row_hi; i += kThreads) {
-                P.d32[i] = fmaf(alpha, P.p32[i], P.d32[i]);
+                P.d32[i] = fmaf(alpha, P.pd32[i], P.d32[i]);
                 const float ri = fmaf(-alpha, P.q32[i], P.r32[i]);
                 P.r32[i] = ri;
                 prr = fmaf(ri, ri, prr);
+                float zi = ri;
                 if (P.precond) {
-                    const float zi = P.dinv32[i] * ri;
-                    P.z32[i] = zi;
+                    zi = P.dinv32[i] * ri;
                     prz = fmaf(ri, zi, prz);
                 }
+                P.p32[i] = zi;   // gathered by the next SpMV (every gather of this one is over)
             }
             double v2[2] = {(double)prr, (double)(P.precond ? prz : prr)};
             block_sum<2>(v2, S);
@@ -558,10 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
             }
             __syncthreads();
             if (!S.ctl[kCtlRun]) break;
-            const float beta = (float)S.bcast[3];
-            for (int i = row_lo + tid; i < row_hi; i += kThreads)
-                P.p32[i] = fmaf(beta, P.p32[i], P.precond ? P.z32[i] : P.r32[i]);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            beta = (float)S.bcast[3];
         }
         // ---- x += d in FP64
         for (int i = row_lo + tid; i < row_hi; i += kThreads) P.x[i] += (double)P.d32[i];
@@ -635,6 +641,7 @@ Params gbcg::base_params(const cg_handle *h) {
     P.z32 = h->z32;
     P.p32 = h->p32;
     P.q32 = h->q32;
+    P.pd32 = h->pd32;
     P.d32 = h->d32;
     P.inner_tol = h->opts.inner_tol;
     P.max_outer = h->opts.max_outer;
@@ -947,6 +954,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
             if ((rc = dev_alloc(h, &h->vals16, (size_t)nnz + 2 * pad))) return fail(rc);
         }
         if ((rc = dev_alloc(h, &h->diag_lo, (size_t)n)) || (rc = dev_alloc(h, &h->r32, (size_t)n)) ||
+            (rc = dev_alloc(h, &h->pd32, (size_t)n)) ||
             (rc = dev_alloc(h, &h->p32, (size_t)n + pad)) || (rc = dev_alloc(h, &h->q32, (size_t)n)) ||
             (rc = dev_alloc(h, &h->d32, (size_t)n)))
             return fail(rc);

@@ -39,6 +39,7 @@ struct cg_handle {
     float *vals32 = nullptr, *diag_lo = nullptr, *dinv32 = nullptr;
     uint16_t *vals16 = nullptr;
     float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+    float *pd32 = nullptr;            // inner direction of the mixed-precision solve
     double *vals = nullptr, *dinv = nullptr;
     double *r = nullptr, *z = nullptr, *p0 = nullptr, *q = nullptr;
     double *pd = nullptr;             // direction of the FP64 CG in memory mode
