@@ -72,6 +72,8 @@ struct BatchParams {
     double *xw;                  // working x, column r at xw + r * xstride (16-byte aligned)
     int32_t xstride;
     float4 *r32, *z32, *p32, *q32, *d32;   // inner vectors, the four right-hand sides interleaved
+                                           // (p32: the vector the SpMM gathers, z)
+    float4 *pd32;                          // inner directions
     double *wpart;               // ctas x warps x kMaxSegPerCta x kSlots: warp partial sums
     double *segpart;             // 2 x nseg x kSlots
     PairState *state;            // ctas x nsys x kRhs
@@ -316,12 +318,15 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                 float4 v = B.r32[i];
                 f4set(v, r, rf);
                 B.r32[i] = v;
-                v = B.z32[i];
-                f4set(v, r, zf);
-                B.z32[i] = v;
                 v = B.p32[i];
                 f4set(v, r, zf);
                 B.p32[i] = v;
+                v = B.pd32[i];
+                f4set(v, r, zf);
+                B.pd32[i] = v;
+                v = B.q32[i];
+                f4set(v, r, 0.0f);
+                B.q32[i] = v;
                 v = B.d32[i];
                 f4set(v, r, 0.0f);
                 B.d32[i] = v;
@@ -365,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     } else {
                         ps.flags = kOuterActive | kInnerActive | kRanInner;
                         ps.rho = rz;
+                        ps.beta = 0.0f;   // p_1 = z_0, q_1 = A z_0
                         ps.target2 = B.inner_tol * B.inner_tol * rr;
                         ps.outer = o + 1;
                         inner_any = 1;
@@ -377,17 +383,25 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                 // ------------------------------------------ inner CG (FP32, 4 rhs)
                 for (int k = 1;; ++k) {
                     auto active = [&](int sys) { return any_flag(sys, kInnerActive); };
-                    // q = A_lo p; p.q
+                    // p = z + beta p, q = A_lo z + beta q (= A_lo p); p.q
+                    // (the SpMM gathers z: A p = A z + beta A p_old)
                     zero_wpart(B);
                     {
                         WarpAcc<float, 4> acc;
                         acc.seg = -1;
                         auto rowfn = [&](int sys, int i, float4 s4, WarpAcc<float, 4> &a) {
+                            const PairState *pp = st + sys * kRhs;
+                            const float b0 = pp[0].beta, b1 = pp[1].beta, b2 = pp[2].beta, b3 = pp[3].beta;
                             const float dg = P.diag_lo[i];
-                            const float4 p = B.p32[i];
-                            const float4 qv = make_float4(fmaf(dg, p.x, s4.x), fmaf(dg, p.y, s4.y),
-                                                          fmaf(dg, p.z, s4.z), fmaf(dg, p.w, s4.w));
+                            const float4 z = B.p32[i], q0 = B.q32[i], p0 = B.pd32[i];
+                            const float4 qv = make_float4(fmaf(b0, q0.x, fmaf(dg, z.x, s4.x)),
+                                                          fmaf(b1, q0.y, fmaf(dg, z.y, s4.y)),
+                                                          fmaf(b2, q0.z, fmaf(dg, z.z, s4.z)),
+                                                          fmaf(b3, q0.w, fmaf(dg, z.w, s4.w)));
+                            const float4 p = make_float4(fmaf(b0, p0.x, z.x), fmaf(b1, p0.y, z.y),
+                                                         fmaf(b2, p0.z, z.z), fmaf(b3, p0.w, z.w));
                             B.q32[i] = qv;
+                            B.pd32[i] = p;
                             a.a[0] = fmaf(p.x, qv.x, a.a[0]);
                             a.a[1] = fmaf(p.y, qv.y, a.a[1]);
                             a.a[2] = fmaf(p.z, qv.z, a.a[2]);
@@ -409,7 +423,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     }
                     __syncthreads();
                     set ^= 1;
-                    // d += alpha p, r -= alpha q, z = dinv r; r.r, r.z
+                    // d += alpha p, r -= alpha q, z = dinv r (gathered by the next SpMM:
+                    // every gather of this one is over); r.r, r.z
                     zero_wpart(B);
                     {
                         WarpAcc<float, 8> acc;
@@ -417,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                         auto rowfn = [&](int sys, int i, float4, WarpAcc<float, 8> &a) {
                             const PairState *pp = st + sys * kRhs;
                             const float al0 = pp[0].alpha, al1 = pp[1].alpha, al2 = pp[2].alpha, al3 = pp[3].alpha;
-                            const float4 p = B.p32[i], qv = B.q32[i];
+                            const float4 p = B.pd32[i], qv = B.q32[i];
                             float4 d = B.d32[i], rv = B.r32[i];
                             d = make_float4(fmaf(al0, p.x, d.x), fmaf(al1, p.y, d.y), fmaf(al2, p.z, d.z),
                                             fmaf(al3, p.w, d.w));
@@ -429,8 +444,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                             if (P.precond) {
                                 const float di = P.dinv32[i];
                                 z = make_float4(di * rv.x, di * rv.y, di * rv.z, di * rv.w);
-                                B.z32[i] = z;
                             }
+                            B.p32[i] = z;
                             a.a[0] = fmaf(rv.x, rv.x, a.a[0]);
                             a.a[1] = fmaf(rv.y, rv.y, a.a[1]);
                             a.a[2] = fmaf(rv.z, rv.z, a.a[2]);
@@ -468,22 +483,6 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     }
                     set ^= 1;
                     if (!__syncthreads_or(left)) break;
-                    // p = z + beta p
-                    {
-                        WarpAcc<float, 0> acc;
-                        acc.seg = -1;
-                        auto rowfn = [&](int sys, int i, float4, WarpAcc<float, 0> &) {
-                            const PairState *pp = st + sys * kRhs;
-                            const float4 z = P.precond ? B.z32[i] : B.r32[i];
-                            const float4 p = B.p32[i];
-                            B.p32[i] = make_float4(fmaf(pp[0].beta, p.x, z.x), fmaf(pp[1].beta, p.y, z.y),
-                                                   fmaf(pp[2].beta, p.z, z.z), fmaf(pp[3].beta, p.w, z.w));
-                        };
-                        if (!batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr, (const float4 *)nullptr,
-                                                            active, rowfn, acc))
-                            goto out;
-                    }
-                    if (!grid_barrier(P, epoch, S)) goto out;
                 }
             }
         }
@@ -555,6 +554,7 @@ struct cg_batch {
     double *vals = nullptr, *xw = nullptr, *wpart = nullptr, *segpart = nullptr;
     float *vals32 = nullptr, *diag_lo = nullptr, *dinv32 = nullptr;
     float4 *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+    float4 *pd32 = nullptr;
     PairState *state = nullptr;
     cg_batch_result *results = nullptr;
     unsigned int *bar = nullptr;
@@ -642,6 +642,7 @@ BatchParams batch_params(const cg_batch *h, const double *Bm, int nrhs, double t
     B.r32 = h->r32;
     B.z32 = h->z32;
     B.p32 = h->p32;
+    B.pd32 = h->pd32;
     B.q32 = h->q32;
     B.d32 = h->d32;
     B.wpart = h->wpart;
@@ -819,6 +820,7 @@ int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in,
         (rc = bdev_alloc(h, &h->sys_seg0, bp.sys_seg0.size())) || (rc = bdev_alloc(h, &h->diag_lo, (size_t)n + 1)) ||
         (rc = bdev_alloc(h, &h->xw, (size_t)kRhs * h->xstride)) ||
         (rc = bdev_alloc(h, &h->r32, (size_t)n + 1)) || (rc = bdev_alloc(h, &h->p32, (size_t)n + pad)) ||
+        (rc = bdev_alloc(h, &h->pd32, (size_t)n + 1)) ||
         (rc = bdev_alloc(h, &h->q32, (size_t)n + 1)) || (rc = bdev_alloc(h, &h->d32, (size_t)n + 1)) ||
         (rc = bdev_alloc(h, &h->wpart, (size_t)ctas * kWarps * kMaxSegPerCta * kSlots)) ||
         (rc = bdev_alloc(h, &h->segpart, (size_t)2 * std::max(h->nseg, 1) * kSlots)) ||
