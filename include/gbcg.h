@@ -146,6 +146,10 @@ typedef struct {
     int32_t reg_rows;        /* rows per thread held in registers (0: none)       */
     int32_t window_tiles;    /* tiles whose gathers read a staged x-window        */
     int64_t device_bytes;    /* device memory the handle owns                     */
+    int32_t slice_solve;     /* 1: FP64 solves run the SELL-32 kernel (one 32-row
+                                slice per warp, 1024 threads per CTA); 0: the
+                                tiled kernel described by the fields above       */
+    int32_t reserved;        /* 0                                                 */
 } cg_plan;
 
 typedef struct cg_handle cg_handle;

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gbcg.cu", "noalloc.cu", "batch.cu", "learn.cu")]
 DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("cg_device.cuh", "layout.h", "plan.h", "lowprec.h",
-                                                           "handle.h")] + [
+                                                           "handle.h", "sell.cuh")] + [
     os.path.join(ROOT, "include", "gbcg.h")]
 OUT = os.path.join(_HERE, "libgbcg.so")
 OBJDIR = os.path.join(_HERE, "_build")

@@ -403,6 +403,347 @@ out:
     drain<double, double>(P, S, pipe, p);
 }
 
+// ------------------------------------------- the SELL-32 solve kernel
+// For systems with at most 31 slices of 32 rows per SM (n <= 150,784 on 152
+// SMs): 1024 threads per CTA, warp w of CTA c owns slice cut[c] + w (a
+// contiguous range balanced by FP64 work on the host) and lane l its row,
+// whose x, r, z, p, q and 1/diag stay in registers.  Warp 31 never owns a
+// slice: it computes 1/rho while the others run the SpMV, so that beta is a
+// product rather than a division on the critical path.  The SpMV
+// reads the SELL-32 copy straight from L2 (every load coalesced), so no warp
+// waits for a shared-memory stage and every warp has at most one slice:
+// phase A costs the FP64 work of one slice per warp.  Same recurrence, stop
+// test and decisions as cg_solve_kernel (two grid barriers per iteration).
+constexpr int kSellSolveThreads = 1024;
+constexpr int kSliceMaxPerCta = kSellSolveThreads / 32 - 1;
+constexpr int kSliceVecCost = 8;   // FP64 vector operations per row, in SpMV-width units
+
+// Sums over the CTA in a fixed order with the FP64 work spread over the four
+// SM sub-partitions (warp w issues on sub-partition w mod 4; one warp-wide
+// FP64 add occupies a sub-partition's FP64 pipe for ~64 cycles, so the number
+// of adds on the busiest sub-partition is the cost).  Quarter g of 32
+// partials per lane is added by warp g and folded by a butterfly; lane j of
+// warp 0 then adds the four quarter sums of value j.  Thread 0 ends with the
+// totals, the same bits in every CTA and every run.
+//
+// Two values share one butterfly: lanes 0-15 fold value 0 and lanes 16-31
+// value 1 after the first exchange.
+template <int NV>
+__device__ __forceinline__ void fold_quarter(double (&t)[NV], double *quarter, int g) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (NV == 2) {
+        const bool lo = lane < 16;
+        const double keep = lo ? t[0] : t[1];
+        double u = keep + __shfl_xor_sync(0xffffffffu, lo ? t[1] : t[0], 16);
+#pragma unroll
+        for (int m = 8; m >= 1; m >>= 1) u += __shfl_xor_sync(0xffffffffu, u, m);
+        if (lane == 0) quarter[g] = u;
+        if (lane == 16) quarter[4 + g] = u;
+    } else {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const double u = warp_sum(t[j]);
+            if (lane == 0) quarter[4 * j + g] = u;
+        }
+    }
+}
+
+// Thread 0 (and every lane of warp 0) gets the totals of the four quarters.
+template <int NV>
+__device__ __forceinline__ void add_quarters(double (&v)[NV], const double *quarter) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    if (lane < NV) {
+        const double *q = quarter + 4 * lane;
+        t = (q[0] + q[1]) + (q[2] + q[3]);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = __shfl_sync(0xffffffffu, t, j);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_1k(double (&v)[NV], double *red, double *quarter) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) red[j * kSellSolveThreads + threadIdx.x] = v[j];
+    __syncthreads();
+    if (w < 4) {
+        double t[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            // 8 partials per lane, added as a tree (depth 3, not a chain of 7)
+            const double *src = red + j * kSellSolveThreads + 32 * w + lane;
+            static_assert(kSellSolveThreads / 128 == 8, "8 partials per lane");
+            t[j] = ((src[0] + src[128]) + (src[256] + src[384])) + ((src[512] + src[640]) + (src[768] + src[896]));
+        }
+        fold_quarter<NV>(t, quarter, w);
+    }
+    __syncthreads();
+    if (w == 0) add_quarters<NV>(v, quarter);
+}
+
+// Grid totals of the partials of barrier set `set`: warp g < 4 adds the
+// partials of CTAs g*32 + lane + 128 u, then as above.  Every CTA computes
+// the same bits.
+template <int NV>
+__device__ __forceinline__ void grid_totals_1k(const Params &P, int set, double (&out)[NV], double *quarter) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int G = (int)gridDim.x;
+    if (w < 4) {
+        const double *src = P.partials + (size_t)set * G * kRedSlots;
+        double t[NV];
+        const int m0 = 32 * w + lane;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) t[j] = m0 < G ? __ldcg(src + (size_t)m0 * kRedSlots + j) : 0.0;
+        for (int m = m0 + 128; m - lane < G; m += 128) {
+#pragma unroll
+            for (int j = 0; j < NV; ++j) t[j] += m < G ? __ldcg(src + (size_t)m * kRedSlots + j) : 0.0;
+        }
+        fold_quarter<NV>(t, quarter, w);
+    }
+    __syncthreads();
+    if (w == 0) add_quarters<NV>(out, quarter);
+}
+
+// Row sum of lane's row in slice t (all 32 lanes of the warp call it).  x is
+// written by this kernel between grid barriers, so its loads are plain
+// coherent loads (L1-cached: the acquire fence of every grid barrier drops
+// stale L1 lines), never the read-only path; the matrix goes through L2 only,
+// leaving L1 to the gathered window of x.
+__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x) {
+    const int lane = threadIdx.x & 31;
+    const bool st = M.stream != 0;
+    const long long a = M.ptr[t];
+    const int w = (int)((M.ptr[t + 1] - a) >> 5);
+    const int row = t * 32 + lane;
+    const double *vv = M.vals + a + lane;
+    double s0 = 0.0, s1 = 0.0;
+    int k = 0;
+    if (M.cols16) {
+        const int16_t *cc = M.cols16 + a + lane;
+        for (; k + kSellUnroll <= w; k += kSellUnroll) {
+            double vr[kSellUnroll], xr[kSellUnroll];
+#pragma unroll
+            for (int u = 0; u < kSellUnroll; ++u) {
+                vr[u] = mload(vv + (k + u) * 32, st);
+                xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
+            }
+#pragma unroll
+            for (int u = 0; u < kSellUnroll; ++u) {
+                if (u & 1) s1 = fma(vr[u], xr[u], s1);
+                else s0 = fma(vr[u], xr[u], s0);
+            }
+        }
+        for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s0);
+    } else {
+        const int32_t *cc = M.cols32 + a + lane;
+        for (; k + kSellUnroll <= w; k += kSellUnroll) {
+            double vr[kSellUnroll], xr[kSellUnroll];
+#pragma unroll
+            for (int u = 0; u < kSellUnroll; ++u) {
+                vr[u] = mload(vv + (k + u) * 32, st);
+                xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
+            }
+#pragma unroll
+            for (int u = 0; u < kSellUnroll; ++u) {
+                if (u & 1) s1 = fma(vr[u], xr[u], s1);
+                else s0 = fma(vr[u], xr[u], s0);
+            }
+        }
+        for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldca(x + mload(cc + k * 32, st)), s0);
+    }
+    return s0 + s1;
+}
+
+template <bool PRE>
+__global__ void __launch_bounds__(kSellSolveThreads, 1)
+    cg_sell_kernel(Params P, SellMatrix M, const int32_t *__restrict__ cut) {
+    __shared__ double red[3 * kSellSolveThreads];
+    __shared__ double quarter[12];
+    __shared__ double bcast[8];
+    __shared__ int ctl[16];
+    Smem S{};
+    S.red = red;
+    S.bcast = bcast;
+    S.ctl = ctl;
+    unsigned int epoch = 0;
+    int set = 0;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int t = cut[blockIdx.x] + w;
+    const bool has_slice = t < cut[blockIdx.x + 1];   // uniform over the warp; never warp 31
+    const int row = t * 32 + lane;
+    const bool own = has_slice && row < P.n;
+    double *const zg = P.p0;   // z, gathered by the SpMV
+
+    // thread 0's scalar state
+    int status = CG_OK, iters = 0;
+    double rr = 0.0, bb = 0.0, true_rr = -1.0, rho = 0.0, bnorm = 0.0, tol2bb = 0.0;
+    // the row's vectors
+    double x = own ? P.x[row] : 0.0, r = 0.0, z = 0.0, p = 0.0, q = 0.0;
+    const double dinv = (own && PRE) ? P.dinv[row] : 1.0;
+
+    // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0; r.r, r.z, b.b
+    bool run;
+    {
+        const double ax = has_slice ? sell_slice_sum(M, t, P.x) : 0.0;
+        double v[3] = {0.0, 0.0, 0.0};
+        if (own) {
+            const double bi = P.b[row];
+            r = bi - ax;
+            z = PRE ? dinv * r : r;
+            p = z;
+            zg[row] = z;
+            v[0] = r * r;
+            v[1] = r * z;
+            v[2] = bi * bi;
+        }
+        block_sum_1k<3>(v, red, quarter);
+        publish_partials<3>(P, set, v);
+        if (!grid_barrier(P, epoch, S)) goto out;
+        double tot[3];
+        grid_totals_1k<3>(P, set, tot, quarter);
+        set ^= 1;
+        if (tid == 0) {
+            rr = tot[0];
+            bb = tot[2];
+            rho = tot[1];
+            bcast[2] = rho;
+            bnorm = sqrt(bb);
+            tol2bb = (P.tol * bnorm) * (P.tol * bnorm);
+            int go = 0, zero_b = 0;
+            if (!finite_bits(bb)) {
+                status = CG_ENAN;
+            } else if (bnorm == 0.0) {
+                rr = 0.0;
+                zero_b = 1;
+            } else if (!finite_bits(rr) || !finite_bits(rho)) {
+                status = CG_ENAN;
+            } else if (rr <= tol2bb) {
+                status = CG_OK;
+            } else if (!(rho > 0.0)) {
+                status = CG_EBREAKDOWN;
+            } else {
+                go = 1;
+            }
+            ctl[kCtlRun] = go;
+            ctl[kCtlZeroB] = zero_b;
+        }
+        __syncthreads();
+        run = ctl[kCtlRun] != 0;
+        if (ctl[kCtlZeroB]) x = 0.0;  // b = 0: the solution is x = 0
+    }
+
+    // ---- the CG loop
+    if (run) {
+        if (tid == 0) status = CG_ENOCONV;
+        double beta = 0.0;
+        for (int k = 1; k <= P.maxit; ++k) {
+            if (tid == kSellSolveThreads - 32) bcast[3] = 1.0 / bcast[2];  // read in phase B's decision
+            // phase A: p = z + beta p, q = A z + beta q (= A p), p . q
+            const double az = has_slice ? sell_slice_sum(M, t, zg) : 0.0;
+            double v1[1] = {0.0};
+            if (own) {
+                q = fma(beta, q, az);
+                p = fma(beta, p, z);
+                v1[0] = p * q;
+            }
+            block_sum_1k<1>(v1, red, quarter);
+            publish_partials<1>(P, set, v1);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double sg[1];
+            grid_totals_1k<1>(P, set, sg, quarter);
+            set ^= 1;
+            if (tid == 0) {
+                const double sigma = sg[0];
+                int go = 0;
+                if (!finite_bits(sigma)) status = CG_ENAN;
+                else if (!(sigma > 0.0)) status = CG_EBREAKDOWN;
+                else go = 1;
+                bcast[0] = go ? rho / sigma : 0.0;
+                ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!ctl[kCtlRun]) break;
+            const double alpha = bcast[0];
+
+            // phase B: x += alpha p, r -= alpha q, z = dinv r (published); r.r, r.z
+            // (plain CG: z = r and r.z = r.r, one sum)
+            constexpr int NB = PRE ? 2 : 1;
+            double v2[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) v2[j] = 0.0;
+            if (own) {
+                x = fma(alpha, p, x);
+                r = fma(-alpha, q, r);
+                z = PRE ? dinv * r : r;
+                zg[row] = z;
+                v2[0] = r * r;
+                if constexpr (PRE) v2[NB - 1] = r * z;
+            }
+            block_sum_1k<NB>(v2, red, quarter);
+            publish_partials<NB>(P, set, v2);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double t2[NB];
+            grid_totals_1k<NB>(P, set, t2, quarter);
+            set ^= 1;
+            if (tid == 0) {
+                iters = k;
+                rr = t2[0];
+                const double rho_new = t2[NB - 1];
+                int go = 0;
+                if (!finite_bits(rr)) status = CG_ENAN;
+                else if (rr <= tol2bb) status = CG_OK;
+                else if (!finite_bits(rho_new)) status = CG_ENAN;
+                else if (!(rho_new > 0.0)) status = CG_EBREAKDOWN;
+                else if (k < P.maxit) go = 1;  // else ENOCONV
+                if (go) {
+                    bcast[1] = rho_new * bcast[3];  // rho_new / rho
+                    rho = rho_new;
+                    bcast[2] = rho;
+                }
+                ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!ctl[kCtlRun]) break;
+            beta = bcast[1];
+        }
+    }
+
+    // ---- publish x, then the true residual ||b - A x||
+    if (own) P.x[row] = x;
+    {
+        if (tid == 0) ctl[kCtlTrue] = (P.true_res && status != CG_ENAN && bb != 0.0) ? 1 : 0;
+        __syncthreads();
+        const bool want_true = ctl[kCtlTrue] != 0;
+        if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
+        if (want_true) {
+            if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
+            const double ax = has_slice ? sell_slice_sum(M, t, P.x) : 0.0;
+            double v[1] = {0.0};
+            if (own) {
+                const double d = P.b[row] - ax;
+                v[0] = d * d;
+            }
+            block_sum_1k<1>(v, red, quarter);
+            publish_partials<1>(P, set, v);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double tt[1];
+            grid_totals_1k<1>(P, set, tt, quarter);
+            if (tid == 0) true_rr = tt[0];
+        }
+    }
+
+    if (blockIdx.x == 0 && tid == 0) {
+        P.st->iters = iters;
+        P.st->rr = rr;
+        P.st->bb = bb;
+        P.st->true_rr = true_rr;
+        atomicCAS(&P.st->status, 0, status);
+    }
+out:
+    return;
+}
+
 // ---------------------------------------------- mixed-precision solve
 // Iterative refinement: the outer loop keeps x and the residual in FP64 with
 // the FP64 matrix (r = b - A x, stop when ||r|| <= tol ||b||, x += d); each
@@ -683,12 +1024,20 @@ int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess) {
-        void *args[] = {&P};
-        const void *kern = (const void *)h->kernel;
-        if (h->opts.inner_values == CG_VALUES_FP32) kern = (const void *)cg_ir_kernel<float>;
-        if (h->opts.inner_values == CG_VALUES_BF16) kern = (const void *)cg_ir_kernel<__nv_bfloat16>;
-        e = cudaLaunchCooperativeKernel(kern, dim3(h->ctas), dim3(kThreads),
-                                        args, (size_t)kSmemBytes, h->stream);
+        if (h->sell_solve && h->opts.inner_values == CG_VALUES_FP64) {
+            SellMatrix M = sell_of(h);
+            const int32_t *cut = h->sell_cut;
+            void *args[] = {&P, &M, &cut};
+            const void *kern = precond ? (const void *)cg_sell_kernel<true> : (const void *)cg_sell_kernel<false>;
+            e = cudaLaunchCooperativeKernel(kern, dim3(h->ctas), dim3(kSellSolveThreads), args, 0, h->stream);
+        } else {
+            void *args[] = {&P};
+            const void *kern = (const void *)h->kernel;
+            if (h->opts.inner_values == CG_VALUES_FP32) kern = (const void *)cg_ir_kernel<float>;
+            if (h->opts.inner_values == CG_VALUES_BF16) kern = (const void *)cg_ir_kernel<__nv_bfloat16>;
+            e = cudaLaunchCooperativeKernel(kern, dim3(h->ctas), dim3(kThreads),
+                                            args, (size_t)kSmemBytes, h->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->stream);
     if (e == cudaSuccess)
@@ -969,6 +1318,33 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         const SellHost sh = build_sell(n, rowptr, colidx, vals);
         h->sell_slices = (n + 31) / 32;
         h->sell_grid = std::max(1, std::min(sms * kSellBlocksPerSm, (h->sell_slices + 7) / 8));
+        // the slice kernel: every warp of the h->ctas CTAs owns at most one slice
+        const std::vector<int32_t> cut =
+            opts.vectors_in_memory || n == 0 ? std::vector<int32_t>{}
+                                             : split_slices(sh.ptr, ctas, kSliceMaxPerCta, kSliceVecCost);
+        h->sell_solve = 0;
+        if (!cut.empty()) {
+            int occ_plain = 0, occ_pre = 0;
+            const bool ok =
+                cudaFuncSetAttribute((const void *)cg_sell_kernel<false>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxL1) == cudaSuccess &&
+                cudaFuncSetAttribute((const void *)cg_sell_kernel<true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxL1) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, cg_sell_kernel<false>,
+                                                              kSellSolveThreads, 0) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pre, cg_sell_kernel<true>,
+                                                              kSellSolveThreads, 0) == cudaSuccess;
+            if (!ok) return fail(CG_ECUDA);
+            if (occ_plain >= 1 && occ_pre >= 1) {
+                if ((rc = dev_alloc(h, &h->sell_cut, cut.size()))) return fail(rc);
+                if (cudaMemcpy(h->sell_cut, cut.data(), sizeof(int32_t) * cut.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                    return fail(CG_ECUDA);
+                h->sell_solve = 1;
+            }
+        }
         const size_t tot = sh.vals.size();
         if ((rc = dev_alloc(h, &h->sell_ptr, sh.ptr.size())) || (rc = dev_alloc(h, &h->sell_vals, tot)))
             return fail(rc);
@@ -1107,6 +1483,7 @@ int cg_get_plan(const cg_handle *h, cg_plan *plan) {
     p.reg_rows = h->rpt;
     p.window_tiles = h->window_tiles;
     p.device_bytes = h->device_bytes;
+    p.slice_solve = h->sell_solve;
     *plan = p;
     return CG_OK;
 }

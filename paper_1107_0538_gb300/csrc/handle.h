@@ -57,6 +57,8 @@ struct cg_handle {
     int32_t *sell_c32 = nullptr;
     int32_t sell_slices = 0;
     int sell_grid = 0;                // CTAs of a SELL SpMV launch
+    int sell_solve = 0;               // 1: FP64 solves run cg_sell_kernel
+    int32_t *sell_cut = nullptr;      // ctas + 1 slice boundaries of the slice kernel's CTAs
 };
 
 namespace gbcg {

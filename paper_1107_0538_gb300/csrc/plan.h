@@ -348,6 +348,43 @@ struct SellHost {
     bool rel16 = true;
 };
 
+// Contiguous slice ranges for the slice solve kernel (one warp per slice): at
+// most max_per_cta slices per CTA and the largest CTA cost as small as
+// possible, the cost of a slice being its width (FP64 FMAs per lane in the
+// SpMV) plus vec_cost (the vector work of its rows).  Binary search on the
+// cost bound with a greedy fill.  Empty when the slices do not fit.
+inline std::vector<int32_t> split_slices(const std::vector<long long> &ptr, int ctas, int max_per_cta,
+                                         long long vec_cost) {
+    const int ns = (int)ptr.size() - 1;
+    if (ns < 0 || ctas < 1 || (long long)ns > (long long)ctas * max_per_cta) return {};
+    std::vector<long long> cost((size_t)ns);
+    long long lo = 0, hi = 0;
+    for (int t = 0; t < ns; ++t) {
+        cost[t] = (ptr[t + 1] - ptr[t]) / 32 + vec_cost;
+        lo = std::max(lo, cost[t]);
+        hi += cost[t];
+    }
+    auto greedy = [&](long long C, std::vector<int32_t> *cut) {
+        int t = 0;
+        for (int c = 0; c < ctas; ++c) {
+            if (cut) (*cut)[c] = t;
+            long long sum = 0;
+            for (int k = 0; t < ns && k < max_per_cta && sum + cost[t] <= C; ++k) sum += cost[t++];
+        }
+        if (cut) (*cut)[ctas] = t;
+        return t == ns;
+    };
+    hi = std::max(hi, lo);
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (greedy(mid, nullptr)) hi = mid;
+        else lo = mid + 1;
+    }
+    std::vector<int32_t> cut((size_t)ctas + 1, 0);
+    greedy(lo, &cut);
+    return cut;
+}
+
 inline SellHost build_sell(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
                            const std::vector<double> &vals) {
     SellHost S;

@@ -72,7 +72,8 @@ class cg_plan(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("l2_evict_first", ctypes.c_int32),
                 ("reg_rows", ctypes.c_int32), ("window_tiles", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("slice_solve", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

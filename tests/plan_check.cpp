@@ -61,6 +61,28 @@ int main(int argc, char **argv) {
             }
         }
     }
+    // slice split of the slice solve kernel (152 CTAs, 31 slices each at most)
+    const int ctas = 152, per = 31;
+    const std::vector<int32_t> cut = gbcg::split_slices(sh.ptr, ctas, per, 8);
+    long long slice_cost = -1, slice_bound = 0, total = 0;
+    if (!cut.empty()) {
+        if ((int)cut.size() != ctas + 1 || cut[0] != 0 || cut[ctas] != ns) sell_err = "slice split bounds";
+        slice_cost = 0;
+        for (int c = 0; c < ctas && sell_err.empty(); ++c) {
+            if (cut[c + 1] < cut[c] || cut[c + 1] - cut[c] > per) sell_err = "slice split range";
+            long long cc = 0;
+            for (int t = cut[c]; t < cut[c + 1]; ++t) cc += (sh.ptr[t + 1] - sh.ptr[t]) / 32 + 8;
+            slice_cost = std::max(slice_cost, cc);
+        }
+        for (int t = 0; t < ns; ++t) {
+            const long long ct = (sh.ptr[t + 1] - sh.ptr[t]) / 32 + 8;
+            total += ct;
+            slice_bound = std::max(slice_bound, ct);
+        }
+        slice_bound = std::max(slice_bound, (total + ctas - 1) / ctas);
+    } else if (ns <= ctas * per) {
+        sell_err = "slice split missing";
+    }
     bool fits = true;
     for (int32_t r = 0; r < n; ++r)
         for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k)
@@ -68,8 +90,8 @@ int main(int argc, char **argv) {
     if (sell_err.empty() && fits != sh.rel16) sell_err = "wrong column width";
     std::printf("{\"tiles\": %d, \"windowed\": %d, \"long\": %d, \"max_tile_nnz\": %d, "
                 "\"max_segments\": %d, \"max_window_tx\": %d, \"sell_entries\": %lld, \"sell_rel16\": %d, "
-                "\"error\": \"%s%s\"}\n",
+                "\"slice_cost\": %lld, \"slice_bound\": %lld, \"error\": \"%s%s\"}\n",
                 nt, tp.windowed, longs, max_nnz, maxseg, maxwin, (long long)sh.ptr.back(), (int)sh.rel16,
-                problem.c_str(), sell_err.c_str());
+                slice_cost, slice_bound, problem.c_str(), sell_err.c_str());
     return problem.empty() && sell_err.empty() ? 0 : 1;
 }

@@ -43,6 +43,8 @@ def problem(name):
             _CACHE[name] = problems.cube_blobs(50)
         elif name == "c3":
             _CACHE[name] = problems.cube_blobs(100)
+        elif name == "c55":
+            _CACHE[name] = problems.cube_blobs(55)
         elif name == "small":
             _CACHE[name] = problems.cube_blobs(7, contrast=1e2, tol=1e-10)
     return _CACHE[name]
@@ -183,6 +185,33 @@ def test_cg_large_fixed_k_and_full_solve(dev):
     assert true <= 1.05 * pr.tol
 
 
+@pytest.mark.parametrize("precond", [0, 1])
+def test_cg_tiled_register_kernel_fixed_k_iterates(dev, precond):
+    """A 55^3 box has more than one 32-row slice per warp, so its solves run
+    the tiled kernel with rows held in registers."""
+    pr = problem("c55")
+    k = 120
+    ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=k, precond=precond)
+    with gbcg.Solver(pr.A, precond=precond) as s:
+        assert s.plan()["slice_solve"] == 0 and s.plan()["reg_rows"] > 0
+    x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=k, precond=precond)
+    assert info.status == gbcg.CG_ENOCONV and info.iters == k == ref["iters"]
+    assert rel(x, ref["x"]) <= 1e-10
+    assert abs(info.relres - ref["relres"]) <= 1e-6 * ref["relres"]
+
+
+def test_slice_kernel_with_fewer_ctas(dev):
+    """grid_ctas limits the slice kernel to 31 slices per CTA: 20^3 (290
+    slices) runs it on 10 CTAs and falls back to the tiled kernel on 8."""
+    pr = problem("c1")
+    ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=60)
+    for ctas, sliced in ((10, 1), (8, 0)):
+        with gbcg.Solver(pr.A, grid_ctas=ctas) as s:
+            assert s.plan()["slice_solve"] == sliced and s.plan()["ctas"] == ctas
+        x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=60, grid_ctas=ctas)
+        assert info.iters == 60 and rel(x, ref["x"]) <= 1e-10
+
+
 # ------------------------------------------------------------- edge cases
 
 @pytest.mark.parametrize("mem", [False, True], ids=["regs", "memory"])
@@ -296,14 +325,18 @@ def test_device_resident_csr_input(dev):
 def test_plan_and_vector_modes(dev):
     with gbcg.Solver(problem("c3").A) as s:
         assert s.plan()["reg_rows"] == 0          # too many rows per thread
+        assert s.plan()["slice_solve"] == 0       # more than one slice per warp
     with gbcg.Solver(problem("c2").A, vectors_in_memory=True) as s:
-        assert s.plan()["reg_rows"] == 0
+        assert s.plan()["reg_rows"] == 0 and s.plan()["slice_solve"] == 0
+    with gbcg.Solver(problem("c55").A) as s:
+        assert s.plan()["slice_solve"] == 0 and s.plan()["reg_rows"] in (1, 2, 4)
     pr = problem("c2")
     with gbcg.Solver(pr.A) as s:
         p = s.plan()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert p["slice_solve"] == (1 if (pr.A.n + 31) // 32 <= 31 * p["ctas"] else 0)
     assert p["reg_rows"] in (1, 2, 4)
     assert p["window_tiles"] == p["tiles"]  # every stencil tile stages its x-window
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
     assert 1 <= p["ctas"] <= sms and p["tiles"] >= p["ctas"]
     assert p["tile_nnz"] <= 896 and p["n"] == pr.A.n and p["nnz"] == pr.A.nnz
 

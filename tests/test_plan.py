@@ -105,3 +105,22 @@ def test_sell_column_widths(checker):
     rowptr, cols = random_pattern(70000, 8)   # random columns reach past 2^15
     out = run_plan(checker, rowptr, cols, 70000)
     assert out["sell_rel16"] == 0
+
+
+def test_slice_split_balances_cost(checker):
+    # contiguous slice ranges, at most 31 slices per CTA, largest CTA cost
+    # between the lower bound (mean, largest slice) and the bound plus one slice
+    e = 20
+    A = problems.q1_matrix(problems.nu_uniform(e, e, e), 1.0 / e)[0]
+    out = run_plan(checker, A.rowptr, A.colidx, A.n)
+    assert out["error"] == ""
+    assert out["slice_bound"] <= out["slice_cost"] <= out["slice_bound"] + 27 + 8
+    # 4713 slices: more than 152 x 31, no split
+    n = 152 * 31 * 32 + 1
+    rowptr = np.arange(n + 1, dtype=np.int32)
+    out = run_plan(checker, rowptr, np.arange(n, dtype=np.int32), n)
+    assert out["error"] == "" and out["slice_cost"] == -1
+    n = 152 * 31 * 32
+    rowptr = np.arange(n + 1, dtype=np.int32)
+    out = run_plan(checker, rowptr, np.arange(n, dtype=np.int32), n)
+    assert out["error"] == "" and out["slice_cost"] == 31 * (1 + 8)
