@@ -88,6 +88,7 @@ def measured_peaks() -> dict:
 _COMMON = ["cg_device.cuh", "layout.h"]
 KERNEL_SOURCES = {
     "cg_solve_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
+    "cg_sell_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
     "sell_spmv_kernel": ["gbcg.cu", "sell.cuh", "plan.h"],
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
@@ -606,9 +607,12 @@ def run_gbcg(args) -> None:
     kern_s = statistics.mean(kern_ms) / 1e3
     achieved_tflops = iters * fpi / kern_s / 1e12
     achieved_gbs = iters * bpi / kern_s / 1e9
-    tr = ncu_traffic("cg_solve_kernel")
+    # the persistent solve kernel the plan picked: one SELL-32 slice per warp
+    # (systems up to 31 slices per CTA) or the tiled kernel
+    solve_kernel = "cg_sell_kernel" if solver.plan()["slice_solve"] else "cg_solve_kernel"
+    tr = ncu_traffic(solve_kernel)
     roofline = {
-        "bound": "alu", "kernel": "cg_solve_kernel", "achieved": round(achieved_tflops, 4),
+        "bound": "alu", "kernel": solve_kernel, "achieved": round(achieved_tflops, 4),
         "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
         "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
         "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
