@@ -43,9 +43,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["gbcg", "reference"], default="gbcg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
-    ap.add_argument("--section", choices=["spmv", "forms", "batched", "batched_full", "learned", "learned_iter"],
+    ap.add_argument("--section", choices=["spmv", "forms", "forms100", "batched", "batched_full", "learned",
+                                          "learned_iter"],
                     help="run one extra section alone and print its JSON: the 100^3 SpMV roofline, the "
-                         "other forms on the 50^3 workload, the 64-system batch, the full 256-system batch, "
+                         "other forms on the 50^3 workload, the forms on the 100^3 system, "
+                         "the 64-system batch, the full 256-system batch, "
                          "the learned preconditioner (training and tests), or the time per flexible-CG "
                          "iteration with an untrained network at 50^3 and 100^3")
     ap.add_argument("--batched-full", action="store_true", help="same as --section batched_full")
@@ -456,6 +458,47 @@ def measure_forms(pr, ms_fp64: float, iters_fp64: int, count: int, x_ref, flush)
     return forms
 
 
+def measure_forms_100cube(flush, count: int = 2) -> dict:
+    """The mixed-precision forms on the 100^3 system (N=1030301, NNZ=27270901,
+    contrast 1e3, b = A x*): the FP64 matrix (327 MB of CSR) no longer fits
+    the L2, so the 8- and 6-byte inner entries of FP32/BF16 refinement cut
+    the bytes each inner iteration streams. ms per solve to rel. residual
+    1e-8, iterations, true residual, and the error against the GPU FP64 CG
+    solution (parity-tested against the oracle) and against x*."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg, problems
+    dev = torch.device("cuda", torch.cuda.current_device())
+    big = problems.cube_blobs(100)
+    b = torch.from_numpy(big.b).to(dev)
+    x = torch.zeros_like(b)
+    out = {"workload": "q1-100^3 blobs (contrast 1e3), N=1030301, NNZ=27270901, b = A x*, x0 = 0, "
+                       "rel. residual 1e-8, L2 flushed before each solve"}
+    x_fp64 = None
+    ms_fp64 = None
+    variants = [("fp64_cg", {}), ("jacobi_pcg", dict(precond=gbcg.CG_PRECOND_JACOBI)),
+                ("fp32_ir", dict(inner_values=gbcg.CG_VALUES_FP32)),
+                ("bf16_ir", dict(inner_values=gbcg.CG_VALUES_BF16)),
+                ("fp32_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI)),
+                ("bf16_ir_jacobi", dict(inner_values=gbcg.CG_VALUES_BF16, precond=gbcg.CG_PRECOND_JACOBI))]
+    for name, kw in variants:
+        vs = gbcg.Solver(big.A, **kw)
+        timed_solves(vs, b, x, 1, flush, False)
+        res_v = timed_solves(vs, b, x, count, flush)
+        v_ms = statistics.mean(t for t, _ in res_v)
+        xv = x.cpu().numpy()
+        info_v = res_v[-1][1]
+        if name == "fp64_cg":
+            x_fp64, ms_fp64 = xv.copy(), v_ms
+        out[name] = {"ms_per_solve": round(v_ms, 3), "iters": info_v.iters, "outer": info_v.outer,
+                     "relres_true": info_v.relres_true,
+                     "err_vs_fp64_cg": float(np.linalg.norm(xv - x_fp64) / np.linalg.norm(x_fp64)),
+                     "err_vs_xstar": float(np.linalg.norm(xv - big.xstar) / np.linalg.norm(big.xstar)),
+                     "speedup_vs_fp64_cg": round(ms_fp64 / v_ms, 3)}
+        vs.close()
+    return out
+
+
 def measure_spmv_hbm(peaks: dict, flush) -> dict:
     """One FP64 SpMV (cg_spmv: the SELL-32 kernel) on the 100^3 system (27.3M
     entries), L2 flushed before each of 20 launches, median time against the
@@ -545,6 +588,8 @@ def run_section(args) -> None:
         res = timed_solves(s, b, x, 3, flush)
         s.close()
         out = measure_forms(pr, statistics.mean(t for t, _ in res), res[-1][1].iters, 3, None, flush)
+    elif name == "forms100":
+        out = measure_forms_100cube(l2_flush_buffer())
     elif name == "batched":
         out = measure_batched(64, 20, 40, 3, tune=True, sample=2)
     elif name == "batched_full":
@@ -674,6 +719,7 @@ def run_gbcg(args) -> None:
                 "sample": f"one full serial FP64 CG solve of the same system ({r['iters']} iterations)"}
         forms = measure_forms(pr, ms_per_step, iters, max(3, args.steps // 2), x_oracle, flush)
         line["spmv_hbm"] = measure_spmv_hbm(peaks, flush)
+        line["forms_100cube"] = measure_forms_100cube(flush)
         line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
         line["learned"] = measure_learned()
         lf = line["learned"]["q1_50cube_c2"]["learned_fcg"]

@@ -505,19 +505,22 @@ __device__ __forceinline__ void grid_totals_1k(const Params &P, int set, double 
     if (w == 0) add_quarters<NV>(out, quarter);
 }
 
-// Row sum of lane's row in slice t (all 32 lanes of the warp call it).  x is
-// written by this kernel between grid barriers, so its loads are plain
-// coherent loads (L1-cached: the acquire fence of every grid barrier drops
-// stale L1 lines), never the read-only path; the matrix goes through L2 only,
-// leaving L1 to the gathered window of x.
-__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x) {
+// init + row sum of lane's row in slice t (all 32 lanes of the warp call it),
+// one accumulator: seven warps per SM sub-partition keep its FP64 pipe busy,
+// so the chain's latency is hidden, and starting from init (beta q in the
+// iteration) saves the separate add of the recurrence.  x is written by this
+// kernel between grid barriers, so its loads are plain coherent loads
+// (L1-cached: the acquire fence of every grid barrier drops stale L1 lines),
+// never the read-only path; the matrix goes through L2 only, leaving L1 to
+// the gathered window of x.
+__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init) {
     const int lane = threadIdx.x & 31;
     const bool st = M.stream != 0;
     const long long a = M.ptr[t];
     const int w = (int)((M.ptr[t + 1] - a) >> 5);
     const int row = t * 32 + lane;
     const double *vv = M.vals + a + lane;
-    double s0 = 0.0, s1 = 0.0;
+    double s = init;
     int k = 0;
     if (M.cols16) {
         const int16_t *cc = M.cols16 + a + lane;
@@ -529,12 +532,9 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
                 xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
             }
 #pragma unroll
-            for (int u = 0; u < kSellUnroll; ++u) {
-                if (u & 1) s1 = fma(vr[u], xr[u], s1);
-                else s0 = fma(vr[u], xr[u], s0);
-            }
+            for (int u = 0; u < kSellUnroll; ++u) s = fma(vr[u], xr[u], s);
         }
-        for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s0);
+        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s);
     } else {
         const int32_t *cc = M.cols32 + a + lane;
         for (; k + kSellUnroll <= w; k += kSellUnroll) {
@@ -545,14 +545,11 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
                 xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
             }
 #pragma unroll
-            for (int u = 0; u < kSellUnroll; ++u) {
-                if (u & 1) s1 = fma(vr[u], xr[u], s1);
-                else s0 = fma(vr[u], xr[u], s0);
-            }
+            for (int u = 0; u < kSellUnroll; ++u) s = fma(vr[u], xr[u], s);
         }
-        for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldca(x + mload(cc + k * 32, st)), s0);
+        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + mload(cc + k * 32, st)), s);
     }
-    return s0 + s1;
+    return s;
 }
 
 template <bool PRE>
@@ -585,7 +582,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0; r.r, r.z, b.b
     bool run;
     {
-        const double ax = has_slice ? sell_slice_sum(M, t, P.x) : 0.0;
+        const double ax = has_slice ? sell_slice_sum(M, t, P.x, 0.0) : 0.0;
         double v[3] = {0.0, 0.0, 0.0};
         if (own) {
             const double bi = P.b[row];
@@ -640,10 +637,9 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         for (int k = 1; k <= P.maxit; ++k) {
             if (tid == kSellSolveThreads - 32) bcast[3] = 1.0 / bcast[2];  // read in phase B's decision
             // phase A: p = z + beta p, q = A z + beta q (= A p), p . q
-            const double az = has_slice ? sell_slice_sum(M, t, zg) : 0.0;
+            if (has_slice) q = sell_slice_sum(M, t, zg, beta * q);
             double v1[1] = {0.0};
             if (own) {
-                q = fma(beta, q, az);
                 p = fma(beta, p, z);
                 v1[0] = p * q;
             }
@@ -718,7 +714,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
         if (want_true) {
             if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
-            const double ax = has_slice ? sell_slice_sum(M, t, P.x) : 0.0;
+            const double ax = has_slice ? sell_slice_sum(M, t, P.x, 0.0) : 0.0;
             double v[1] = {0.0};
             if (own) {
                 const double d = P.b[row] - ax;
