@@ -405,17 +405,21 @@ out:
 
 // ------------------------------------------- the SELL-32 solve kernel
 // For systems with at most 31 slices of 32 rows per SM (n <= 150,784 on 152
-// SMs): 1024 threads per CTA, warp w of CTA c owns slice cut[c] + w (a
-// contiguous range balanced by FP64 work on the host) and lane l its row,
-// whose x, r, z, p, q and 1/diag stay in registers.  Warp 31 never owns a
-// slice: it computes 1/rho while the others run the SpMV, so that beta is a
-// product rather than a division on the critical path.  The SpMV
-// reads the SELL-32 copy straight from L2 (every load coalesced), so no warp
-// waits for a shared-memory stage and every warp has at most one slice:
-// phase A costs the FP64 work of one slice per warp.  Same recurrence, stop
-// test and decisions as cg_solve_kernel (two grid barriers per iteration).
+// SMs): 1024 threads per CTA.  Warp 0 is the control warp and owns no slice;
+// warp w >= 1 of CTA c owns slice cut[c] + w - 1 (contiguous ranges balanced
+// by FP64 work on the host) and lane l its row, whose x, r, z, p, q and
+// 1/diag stay in registers.  The SpMV reads the SELL-32 copy straight from L2
+// (every load coalesced), so no warp waits for a shared-memory stage and
+// every warp has at most one slice.
+//
+// Two grid barriers per iteration, as in cg_solve_kernel, with one change of
+// order: the SpMV A z of iteration k+1 needs only z, so it starts as soon as
+// the barrier that publishes z has passed, and the control warp meanwhile
+// adds the grid totals of r.r and r.z, takes the stop decision and forms
+// beta = rho'/rho.  The warps then finish q = A z + beta q and p = z + beta p
+// (the last iteration's SpMV is computed and dropped).
 constexpr int kSellSolveThreads = 1024;
-constexpr int kSliceMaxPerCta = kSellSolveThreads / 32 - 1;
+constexpr int kSliceMaxPerCta = kSellSolveThreads / 32 - 1;   // warps 1..31
 constexpr int kSliceVecCost = 8;   // FP64 vector operations per row, in SpMV-width units
 
 // Sums over the CTA in a fixed order with the FP64 work spread over the four
@@ -566,8 +570,8 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     unsigned int epoch = 0;
     int set = 0;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int t = cut[blockIdx.x] + w;
-    const bool has_slice = t < cut[blockIdx.x + 1];   // uniform over the warp; never warp 31
+    const int t = cut[blockIdx.x] + w - 1;
+    const bool has_slice = w >= 1 && t < cut[blockIdx.x + 1];   // uniform over the warp; never warp 0
     const int row = t * 32 + lane;
     const bool own = has_slice && row < P.n;
     double *const zg = P.p0;   // z, gathered by the SpMV
@@ -604,7 +608,6 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             rr = tot[0];
             bb = tot[2];
             rho = tot[1];
-            bcast[2] = rho;
             bnorm = sqrt(bb);
             tol2bb = (P.tol * bnorm) * (P.tol * bnorm);
             int go = 0, zero_b = 0;
@@ -633,13 +636,41 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     // ---- the CG loop
     if (run) {
         if (tid == 0) status = CG_ENOCONV;
-        double beta = 0.0;
-        for (int k = 1; k <= P.maxit; ++k) {
-            if (tid == kSellSolveThreads - 32) bcast[3] = 1.0 / bcast[2];  // read in phase B's decision
-            // phase A: p = z + beta p, q = A z + beta q (= A p), p . q
-            if (has_slice) q = sell_slice_sum(M, t, zg, beta * q);
+        constexpr int NB = PRE ? 2 : 1;
+        // thread 0: decision on the r.r, r.z totals of iteration kk (recorded
+        // in kk's exchange); go = 1 sets beta for the next iteration
+        auto decide = [&](int kk, const double (&t2)[NB]) {
+            iters = kk;
+            rr = t2[0];
+            const double rho_new = t2[NB - 1];
+            int go = 0;
+            if (!finite_bits(rr)) status = CG_ENAN;
+            else if (rr <= tol2bb) status = CG_OK;
+            else if (!finite_bits(rho_new)) status = CG_ENAN;
+            else if (!(rho_new > 0.0)) status = CG_EBREAKDOWN;
+            else if (kk < P.maxit) go = 1;  // else ENOCONV
+            if (go) {
+                bcast[1] = rho_new / rho;
+                rho = rho_new;
+            }
+            ctl[kCtlRun] = go;
+        };
+        for (int k = 1;; ++k) {
+            // phase A: az = A z on warps 1..31; the control warp decides on
+            // iteration k-1 meanwhile
+            const double az = has_slice ? sell_slice_sum(M, t, zg, 0.0) : 0.0;
+            if (k > 1 && w == 0) {
+                double t2[NB];
+                grid_totals<NB>(P, set ^ 1, t2);
+                if (tid == 0) decide(k - 1, t2);
+            }
+            __syncthreads();
+            if (k > 1 && !ctl[kCtlRun]) break;
+            const double beta = k > 1 ? bcast[1] : 0.0;
+            // p = z + beta p, q = A z + beta q (= A p), p . q
             double v1[1] = {0.0};
             if (own) {
+                q = fma(beta, q, az);
                 p = fma(beta, p, z);
                 v1[0] = p * q;
             }
@@ -664,7 +695,6 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
 
             // phase B: x += alpha p, r -= alpha q, z = dinv r (published); r.r, r.z
             // (plain CG: z = r and r.z = r.r, one sum)
-            constexpr int NB = PRE ? 2 : 1;
             double v2[NB];
 #pragma unroll
             for (int j = 0; j < NB; ++j) v2[j] = 0.0;
@@ -679,29 +709,16 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             block_sum_1k<NB>(v2, red, quarter);
             publish_partials<NB>(P, set, v2);
             if (!grid_barrier(P, epoch, S)) goto out;
-            double t2[NB];
-            grid_totals_1k<NB>(P, set, t2, quarter);
-            set ^= 1;
-            if (tid == 0) {
-                iters = k;
-                rr = t2[0];
-                const double rho_new = t2[NB - 1];
-                int go = 0;
-                if (!finite_bits(rr)) status = CG_ENAN;
-                else if (rr <= tol2bb) status = CG_OK;
-                else if (!finite_bits(rho_new)) status = CG_ENAN;
-                else if (!(rho_new > 0.0)) status = CG_EBREAKDOWN;
-                else if (k < P.maxit) go = 1;  // else ENOCONV
-                if (go) {
-                    bcast[1] = rho_new * bcast[3];  // rho_new / rho
-                    rho = rho_new;
-                    bcast[2] = rho;
+            set ^= 1;   // this exchange's partials are set ^ 1 from here on
+            if (k == P.maxit) {   // the last allowed iteration: decide now
+                if (w == 0) {
+                    double t2[NB];
+                    grid_totals<NB>(P, set ^ 1, t2);
+                    if (tid == 0) decide(k, t2);
                 }
-                ctl[kCtlRun] = go;
+                __syncthreads();
+                break;
             }
-            __syncthreads();
-            if (!ctl[kCtlRun]) break;
-            beta = bcast[1];
         }
     }
 
