@@ -281,27 +281,37 @@ __device__ __forceinline__ bool finite_bits(double v) {
 // write before the barrier visible to every read after it.  The wait is
 // bounded by P.wait_ns; on timeout the error is recorded and false returned
 // by every thread of the CTA.
-__device__ __forceinline__ bool grid_barrier(const Params &P, unsigned int &epoch, const Smem &S) {
+// The barrier in two halves, for a CTA that works while it waits: every
+// thread calls grid_arrive (after the writes the barrier publishes), thread 0
+// alone calls grid_wait (the bounded wait; 1 = passed), and a __syncthreads
+// after it releases the CTA.
+__device__ __forceinline__ void grid_arrive(const Params &P, unsigned int &epoch) {
     __syncthreads();
     ++epoch;
-    if (threadIdx.x == 0) {
-        const unsigned int target = epoch * (gridDim.x + (unsigned)P.phantom);
-        red_release_add(P.bar, 1u);
-        int ok = 1;
-        if (ld_acquire(P.bar) < target) {
-            const unsigned long long t0 = global_ns();
-            unsigned int spins = 0;
-            while (ld_acquire(P.bar) < target) {
-                if ((++spins & 63u) == 0 && global_ns() - t0 > P.wait_ns) {
-                    ok = 0;
-                    break;
-                }
+    if (threadIdx.x == 0) red_release_add(P.bar, 1u);
+}
+
+__device__ __forceinline__ int grid_wait(const Params &P, unsigned int epoch) {
+    const unsigned int target = epoch * (gridDim.x + (unsigned)P.phantom);
+    int ok = 1;
+    if (ld_acquire(P.bar) < target) {
+        const unsigned long long t0 = global_ns();
+        unsigned int spins = 0;
+        while (ld_acquire(P.bar) < target) {
+            if ((++spins & 63u) == 0 && global_ns() - t0 > P.wait_ns) {
+                ok = 0;
+                break;
             }
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        if (!ok) set_error(P.st, CG_ETIMEOUT, 1);
-        S.ctl[15] = ok;
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    if (!ok) set_error(P.st, CG_ETIMEOUT, 1);
+    return ok;
+}
+
+__device__ __forceinline__ bool grid_barrier(const Params &P, unsigned int &epoch, const Smem &S) {
+    grid_arrive(P, epoch);
+    if (threadIdx.x == 0) S.ctl[15] = grid_wait(P, epoch);
     __syncthreads();
     return S.ctl[15] != 0;
 }

@@ -517,15 +517,17 @@ __device__ __forceinline__ void grid_totals_1k(const Params &P, int set, double 
 // (L1-cached: the acquire fence of every grid barrier drops stale L1 lines),
 // never the read-only path; the matrix goes through L2 only, leaving L1 to
 // the gathered window of x.
-__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init) {
+// Entries k0 <= k < k1 of the slice (k1 < 0: to the slice width).
+__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init,
+                                                 int k0 = 0, int k1 = -1) {
     const int lane = threadIdx.x & 31;
     const bool st = M.stream != 0;
     const long long a = M.ptr[t];
-    const int w = (int)((M.ptr[t + 1] - a) >> 5);
+    const int w = k1 >= 0 ? k1 : (int)((M.ptr[t + 1] - a) >> 5);
     const int row = t * 32 + lane;
     const double *vv = M.vals + a + lane;
     double s = init;
-    int k = 0;
+    int k = k0;
     if (M.cols16) {
         const int16_t *cc = M.cols16 + a + lane;
         for (; k + kSellUnroll <= w; k += kSellUnroll) {
@@ -655,10 +657,15 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             ctl[kCtlRun] = go;
         };
+        // each slice's entries in this CTA's own rows come first (k < wl); the
+        // first iteration's are added here, the others' while the barrier
+        // that publishes z completes
+        const int wl = has_slice ? (M.split ? M.split[t] : 0) : 0;
+        double azl = has_slice ? sell_slice_sum(M, t, zg, 0.0, 0, wl) : 0.0;
         for (int k = 1;; ++k) {
-            // phase A: az = A z on warps 1..31; the control warp decides on
-            // iteration k-1 meanwhile
-            const double az = has_slice ? sell_slice_sum(M, t, zg, 0.0) : 0.0;
+            // phase A: az = A z on warps 1..31 (the rest of each row, from
+            // azl); the control warp decides on iteration k-1 meanwhile
+            const double az = has_slice ? sell_slice_sum(M, t, zg, azl, wl) : 0.0;
             if (k > 1 && w == 0) {
                 double t2[NB];
                 grid_totals<NB>(P, set ^ 1, t2);
@@ -708,7 +715,14 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<NB>(v2, red, quarter);
             publish_partials<NB>(P, set, v2);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            // the barrier that publishes z: the warps with a slice add its
+            // entries in this CTA's own rows (z written before grid_arrive's
+            // __syncthreads) while thread 0 waits for the other CTAs
+            grid_arrive(P, epoch);
+            if (has_slice) azl = sell_slice_sum(M, t, zg, 0.0, 0, wl);
+            else if (tid == 0) ctl[15] = grid_wait(P, epoch);
+            __syncthreads();
+            if (!ctl[15]) goto out;
             set ^= 1;   // this exchange's partials are set ^ 1 from here on
             if (k == P.maxit) {   // the last allowed iteration: decide now
                 if (w == 0) {
@@ -1327,8 +1341,8 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
             h->z32 = h->r32;
         }
     }
-    {   // SELL-32 copy for the stand-alone SpMV
-        const SellHost sh = build_sell(n, rowptr, colidx, vals);
+    {   // SELL-32 copy for the stand-alone SpMV and the slice solve kernel
+        SellHost sh = build_sell(n, rowptr, colidx, vals);
         h->sell_slices = (n + 31) / 32;
         h->sell_grid = std::max(1, std::min(sms * kSellBlocksPerSm, (h->sell_slices + 7) / 8));
         // the slice kernel: every warp of the h->ctas CTAs owns at most one slice
@@ -1351,9 +1365,16 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
                                                               kSellSolveThreads, 0) == cudaSuccess;
             if (!ok) return fail(CG_ECUDA);
             if (occ_plain >= 1 && occ_pre >= 1) {
-                if ((rc = dev_alloc(h, &h->sell_cut, cut.size()))) return fail(rc);
+                // each row's entries in the CTA's own rows first (read while the
+                // grid barrier that publishes z completes)
+                sh = build_sell(n, rowptr, colidx, vals, &cut);
+                if ((rc = dev_alloc(h, &h->sell_cut, cut.size())) ||
+                    (rc = dev_alloc(h, &h->sell_split, sh.split.size())))
+                    return fail(rc);
                 if (cudaMemcpy(h->sell_cut, cut.data(), sizeof(int32_t) * cut.size(), cudaMemcpyHostToDevice) !=
-                    cudaSuccess)
+                        cudaSuccess ||
+                    cudaMemcpy(h->sell_split, sh.split.data(), sizeof(int32_t) * sh.split.size(),
+                               cudaMemcpyHostToDevice) != cudaSuccess)
                     return fail(CG_ECUDA);
                 h->sell_solve = 1;
             }

@@ -59,6 +59,7 @@ struct cg_handle {
     int sell_grid = 0;                // CTAs of a SELL SpMV launch
     int sell_solve = 0;               // 1: FP64 solves run cg_sell_kernel
     int32_t *sell_cut = nullptr;      // ctas + 1 slice boundaries of the slice kernel's CTAs
+    int32_t *sell_split = nullptr;    // per slice: local block width (split layout), or nullptr
 };
 
 namespace gbcg {
@@ -94,7 +95,8 @@ struct DeviceGuard {
 Params base_params(const cg_handle *h);
 // The handle's SELL-32 matrix.
 inline SellMatrix sell_of(const cg_handle *h) {
-    return SellMatrix{h->n, h->sell_slices, h->evict_first, h->sell_ptr, h->sell_vals, h->sell_c16, h->sell_c32};
+    return SellMatrix{h->n,        h->sell_slices, h->evict_first, h->sell_ptr,
+                      h->sell_vals, h->sell_c16,    h->sell_c32,     h->sell_split};
 }
 // Enqueues one persistent FP64 CG solve with the given preconditioner flag
 // (0 plain, 1 Jacobi) on the handle's stream, without synchronizing (gbcg.cu).

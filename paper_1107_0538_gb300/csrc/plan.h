@@ -339,12 +339,18 @@ inline std::string check_plan(int32_t n, const std::vector<int32_t> &rowptr,
 
 // SELL-32 copy of a CSR matrix (see sell.cuh): slices of 32 rows padded to
 // their longest row, entries k-major within a slice; 16-bit column offsets
-// from the row when all fit, else 32-bit columns.
+// from the row when all fit, else 32-bit columns.  With a slice split (the
+// CTA slice ranges of the slice solve kernel), each row's entries whose
+// column lies in its CTA's own rows come first (CSR order), padded to the
+// slice's local width split[t], then the others (CSR order), padded to the
+// slice width; padding entries are zeros at the row itself (n - 1 past n),
+// which is always one of the CTA's own rows.
 struct SellHost {
     std::vector<long long> ptr;
     std::vector<double> vals;
     std::vector<int16_t> cols16;
     std::vector<int32_t> cols32;
+    std::vector<int32_t> split;   // local width per slice (split layout only)
     bool rel16 = true;
 };
 
@@ -386,13 +392,46 @@ inline std::vector<int32_t> split_slices(const std::vector<long long> &ptr, int 
 }
 
 inline SellHost build_sell(int32_t n, const std::vector<int32_t> &rowptr, const std::vector<int32_t> &colidx,
-                           const std::vector<double> &vals) {
+                           const std::vector<double> &vals, const std::vector<int32_t> *slice_cut = nullptr) {
     SellHost S;
     const int ns = (n + 31) / 32;
+    // entry order of each row: local entries first when split
+    std::vector<int32_t> order(rowptr.empty() ? 0 : (size_t)rowptr[n]);
+    std::vector<int32_t> nloc((size_t)n, 0);
+    std::vector<int32_t> row_lo((size_t)ns, 0), row_hi((size_t)ns, n);
+    if (slice_cut) {
+        const int ctas = (int)slice_cut->size() - 1;
+        for (int c = 0; c < ctas; ++c)
+            for (int t = (*slice_cut)[c]; t < (*slice_cut)[c + 1]; ++t) {
+                row_lo[t] = (*slice_cut)[c] * 32;
+                row_hi[t] = std::min(n, (*slice_cut)[c + 1] * 32);
+            }
+    }
+    for (int32_t r = 0; r < n; ++r) {
+        const int t = r / 32;
+        int32_t o = rowptr[r];
+        for (int pass = 0; pass < (slice_cut ? 2 : 1); ++pass)
+            for (int32_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+                const bool local = colidx[k] >= row_lo[t] && colidx[k] < row_hi[t];
+                if (slice_cut && local != (pass == 0)) continue;
+                order[o++] = k;
+                if (slice_cut && local) ++nloc[r];
+            }
+    }
     S.ptr.assign((size_t)ns + 1, 0);
+    if (slice_cut) S.split.assign((size_t)ns, 0);
     for (int t = 0; t < ns; ++t) {
-        int w = 0;
-        for (int r = t * 32; r < std::min(n, t * 32 + 32); ++r) w = std::max(w, rowptr[r + 1] - rowptr[r]);
+        int w = 0, wl = 0, wr = 0;
+        for (int r = t * 32; r < std::min(n, t * 32 + 32); ++r) {
+            const int len = rowptr[r + 1] - rowptr[r];
+            w = std::max(w, len);
+            wl = std::max(wl, nloc[r]);
+            wr = std::max(wr, len - nloc[r]);
+        }
+        if (slice_cut) {
+            S.split[t] = wl;
+            w = wl + wr;
+        }
         S.ptr[t + 1] = S.ptr[t] + 32LL * w;
     }
     const size_t tot = (size_t)S.ptr[ns];
@@ -409,15 +448,25 @@ inline SellHost build_sell(int32_t n, const std::vector<int32_t> &rowptr, const 
     else S.cols32.assign(tot, 0);
     for (int t = 0; t < ns; ++t) {
         const int w = (int)((S.ptr[t + 1] - S.ptr[t]) / 32);
+        const int wl = slice_cut ? S.split[t] : w;
         for (int l = 0; l < 32; ++l) {
             const int r = t * 32 + l;
+            const int len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
+            const int nl = slice_cut ? (r < n ? nloc[r] : 0) : len;
             for (int k = 0; k < w; ++k) {
                 const size_t idx = (size_t)S.ptr[t] + (size_t)k * 32 + l;
-                int col = r < n ? r : n - 1;   // padding: value 0 at an in-range column
+                int col = r < n ? r : n - 1;   // padding: value 0 at one of the CTA's own rows
                 double v = 0.0;
-                if (r < n && k < rowptr[r + 1] - rowptr[r]) {
-                    col = colidx[rowptr[r] + k];
-                    v = vals[rowptr[r] + k];
+                int e = -1;   // position in the row's entry order
+                if (k < wl) {
+                    if (k < nl) e = k;
+                } else if (k - wl < len - nl) {
+                    e = nl + (k - wl);
+                }
+                if (r < n && e >= 0) {
+                    const int32_t src = order[rowptr[r] + e];
+                    col = colidx[src];
+                    v = vals[src];
                 }
                 S.vals[idx] = v;
                 if (S.rel16) S.cols16[idx] = (int16_t)(col - r);

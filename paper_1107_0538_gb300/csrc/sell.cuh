@@ -27,6 +27,8 @@ struct SellMatrix {
     const double *__restrict__ vals;       // padded entries
     const int16_t *__restrict__ cols16;    // col - row, or nullptr
     const int32_t *__restrict__ cols32;    // col, when cols16 is nullptr
+    const int32_t *__restrict__ split;     // per slice: width of the block of entries in the CTA's own
+                                           // rows (slice solve kernel layout), or nullptr
 };
 
 constexpr int kSellThreads = 256;

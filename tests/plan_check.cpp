@@ -4,6 +4,7 @@
 // check_plan on the result, builds the SELL-32 copy and checks that every
 // stored entry decodes back to its CSR entry and every padded entry is a
 // zero at an in-range column; prints a one-line JSON summary.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -80,6 +81,42 @@ int main(int argc, char **argv) {
             slice_bound = std::max(slice_bound, ct);
         }
         slice_bound = std::max(slice_bound, (total + ctas - 1) / ctas);
+        // the split layout: every entry of a slice's local block (padding too)
+        // lies in the CTA's own rows; each row keeps exactly its CSR entries
+        const gbcg::SellHost sp = gbcg::build_sell(n, rowptr, colidx, vals, &cut);
+        if ((int)sp.ptr.size() != ns + 1 || (int)sp.split.size() != ns || sp.rel16 != sh.rel16)
+            sell_err = "split layout sizes";
+        for (int c = 0; c < ctas && sell_err.empty(); ++c) {
+            const int r0 = cut[c] * 32, r1 = std::min(n, cut[c + 1] * 32);
+            for (int t = cut[c]; t < cut[c + 1] && sell_err.empty(); ++t) {
+                const int w = (int)((sp.ptr[t + 1] - sp.ptr[t]) / 32);
+                if (sp.split[t] < 0 || sp.split[t] > w) { sell_err = "split width"; break; }
+                for (int l = 0; l < 32 && sell_err.empty(); ++l) {
+                    const int r = t * 32 + l;
+                    std::vector<long long> seen;
+                    for (int k = 0; k < w; ++k) {
+                        const size_t idx = (size_t)sp.ptr[t] + (size_t)k * 32 + l;
+                        const int col = sp.rel16 ? r + sp.cols16[idx] : sp.cols32[idx];
+                        if (col < 0 || col >= n) { sell_err = "split column out of range"; break; }
+                        if (k < sp.split[t] && (col < r0 || col >= r1)) { sell_err = "remote column in local block"; break; }
+                        const double v = sp.vals[idx];
+                        if (v == 0.0) continue;
+                        const long long e = (long long)v - 1;
+                        if (r >= n || e < rowptr[r] || e >= rowptr[r + 1] || colidx[e] != col) {
+                            sell_err = "split entry does not decode";
+                            break;
+                        }
+                        seen.push_back(e);
+                    }
+                    if (!sell_err.empty()) break;
+                    std::sort(seen.begin(), seen.end());
+                    const long long len = r < n ? rowptr[r + 1] - rowptr[r] : 0;
+                    bool ok = (long long)seen.size() == len;
+                    for (long long i = 0; ok && i < len; ++i) ok = seen[i] == rowptr[r] + i;
+                    if (!ok) sell_err = "split row entries";
+                }
+            }
+        }
     } else if (ns <= ctas * per) {
         sell_err = "slice split missing";
     }
