@@ -583,7 +583,9 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     double rr = 0.0, bb = 0.0, true_rr = -1.0, rho = 0.0, bnorm = 0.0, tol2bb = 0.0;
     // the row's vectors
     double x = own ? P.x[row] : 0.0, r = 0.0, z = 0.0, p = 0.0, q = 0.0;
-    const double dinv = (own && PRE) ? P.dinv[row] : 1.0;
+    // 1/diag is read from memory (L1) where it is used: a register for it
+    // makes the Jacobi instantiation spill
+    const double *__restrict__ dinv_g = P.dinv;
 
     // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0; r.r, r.z, b.b
     bool run;
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         if (own) {
             const double bi = P.b[row];
             r = bi - ax;
-            z = PRE ? dinv * r : r;
+            z = PRE ? __ldg(dinv_g + row) * r : r;
             p = z;
             zg[row] = z;
             v[0] = r * r;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             if (own) {
                 x = fma(alpha, p, x);
                 r = fma(-alpha, q, r);
-                z = PRE ? dinv * r : r;
+                z = PRE ? __ldg(dinv_g + row) * r : r;
                 zg[row] = z;
                 v2[0] = r * r;
                 if constexpr (PRE) v2[NB - 1] = r * z;

@@ -71,6 +71,7 @@ struct Geo {
     int px, py, pz;       // padded extents
     int plane;            // px * py
     int bx, by, bz, tiles;
+    int tbx, tby, tbz, ttiles;   // bricks of the tensor-core 16 -> 16 convolution
     int n;                // nodes
     long long npad;       // px py pz
 };
@@ -88,6 +89,10 @@ Geo make_geo(int ex, int ey, int ez) {
     G.by = (G.ny + kBY - 1) / kBY;
     G.bz = (G.nz + kBZ - 1) / kBZ;
     G.tiles = G.bx * G.by * G.bz;
+    G.tbx = (G.nx + 7) / 8;
+    G.tby = (G.ny + 15) / 16;
+    G.tbz = (G.nz + 3) / 4;
+    G.ttiles = G.tbx * G.tby * G.tbz;
     G.n = G.nx * G.ny * G.nz;
     G.npad = (long long)G.px * G.py * G.pz;
     return G;
@@ -246,6 +251,8 @@ struct ConvArgs {
     double *partials;
     FcgState *st;                // solver state (nullptr: always run; conv1 scales by sigma[1] if set)
     const double *sigma;         // apply: {sigma, 1/sigma}: conv1 output scale, conv_out output scale
+    unsigned long long wait_ns;  // bound of the tensor-core kernel's wait for its MMAs
+    int *err;                    // that kernel's timeout report when st is nullptr (or nullptr)
 };
 
 enum { E_STORE = 0, E_GATE = 1, E_GATE_PRE = 2, E_BWD_GATE = 3, E_SIGMOID = 4 };
@@ -361,6 +368,197 @@ __global__ void __launch_bounds__(kCT, 3) conv16_kernel(ConvArgs A) {
         }
     }
     store16<EPI>(A, B, w, acc, gv, 1.0f);
+}
+
+// ------------------------------------ 16 -> 16 convolution on tcgen05
+// The convolution of conv16_kernel (E_STORE, E_GATE: the flexible-CG body and
+// the stand-alone apply) on the 5th-generation tensor cores.  A CTA owns a
+// brick of 8 (x) x 16 (y) x 4 (z) outputs.  Its input with the halo (10 x 18
+// x 6 positions) is staged channel-split: channels 0-7 of every position in
+// one plane of 16-byte rows, channels 8-15 in a second plane.  The 128
+// outputs of a z-plane of the brick (x fastest, 8 per y) then form an
+// M = 128 operand in the canonical K-major layout without swizzle: 8-row
+// core matrices of consecutive x, 16 bytes per row, y groups one staged row
+// (160 bytes) apart, the two K halves one plane apart.  Tap (dx, dy, dz) is
+// the same operand moved by dx + 10 dy + 180 dz positions, so each of the 27
+// taps is one MMA (M = 128, N = 16, K = 16; BF16 in, FP32 accumulate) into
+// the plane's 16 TMEM columns: 108 MMAs per brick, issued by one thread per
+// plane, completing on an mbarrier.  Warps w and w + 4 read TMEM lanes
+// 32 (w mod 4) .. + 31 (output i = lane index) of alternate planes.
+constexpr int kTX = 8, kTY = 16, kTZ = 4;
+constexpr int kTSX = kTX + 2, kTSY = kTY + 2, kTSZ = kTZ + 2;
+constexpr int kTStaged = kTSX * kTSY * kTSZ;                  // 1080 positions
+constexpr uint32_t kTPlane = (uint32_t)kTStaged * 16;          // bytes of one channel half
+constexpr uint32_t kTWeights = (uint32_t)kTaps * kCh * kCh * 2;  // 13824 bytes
+constexpr uint32_t kTCols = 64;                                // TMEM columns: 4 planes x 16
+static_assert(kTX * kTY == 128, "one M = 128 operand per z-plane");
+size_t conv16tc_smem(const Geo &) { return 2 * (size_t)kTPlane + kTWeights + 16; }
+
+// Shared-memory matrix descriptor (SM100 version 1), no swizzle: start, LBO
+// (K-direction core-matrix stride) and SBO (M/N-direction 8-row group
+// stride), each in 16-byte units.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major,
+// N = 16 (bits 17-22: N / 8), M = 128 (bits 24-28: M / 16).
+constexpr uint32_t kConvIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void finish(FcgState *st, int status);
+
+template <int EPI>
+__global__ void __launch_bounds__(kCT) conv16tc_kernel(ConvArgs A) {
+    static_assert(EPI == E_STORE || EPI == E_GATE, "forward epilogues only");
+    if (conv_skip(A.st)) return;
+    extern __shared__ __align__(128) unsigned char sm[];
+    const Geo &G = A.G;
+    unsigned char *sw = sm + 2 * kTPlane;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sw + kTWeights);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tile = blockIdx.x, rest = tile / G.tbx;
+    const int x0 = (tile % G.tbx) * kTX, y0 = (rest % G.tby) * kTY, z0 = (rest / G.tby) * kTZ;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // input with halo: staged position (xs, ys, zs) is padded node
+    // (x0 + xs, y0 + ys, z0 + zs); rows past the padded grid are zero.  A
+    // warp copies one staged row (10 positions: 320 contiguous bytes) at a
+    // time, lane l < 20 one 16-byte chunk.
+    {
+        const int xs = lane >> 1, h = lane & 1;
+        for (int row = w; row < kTSY * kTSZ; row += kCT / 32) {
+            if (lane >= 2 * kTSX) continue;
+            const int ys = row % kTSY, zs = row / kTSY;
+            const int py = y0 + ys, pz = z0 + zs;
+            unsigned char *dst = sm + h * kTPlane + (uint32_t)(row * kTSX + xs) * 16;
+            if (py < G.py && pz < G.pz)
+                cp_async16(dst, A.in + ((long long)pz * G.plane + (long long)py * G.px + x0 + xs) * kCh + h * 8);
+            else
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    // weights of tap t: B = K[t] as 16 (N = output) rows of 16 (K = input)
+    // channels, K halves 256 bytes apart, 8-row groups 128 bytes apart; a
+    // warp copies one tap (32 chunks) at a time
+    for (int t = w; t < kTaps; t += kCT / 32) {
+        const int o = lane >> 1, h = lane & 1;
+        cp_async16(sw + t * 512 + h * 256 + o * 16, A.w + ((size_t)t * kCh + o) * kCh + h * 8);
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(kTCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 32) {
+        mbar_init(bar, kTZ);   // one commit per issuing warp
+        mbar_init_fence();
+    }
+    // gates of this thread's outputs, loaded while the MMAs run
+    uint4 gq[2][2];
+    const int i = 32 * (w & 3) + lane;   // output (M row, TMEM lane) of this thread
+    const int ox = x0 + (i & 7), oy = y0 + (i >> 3);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int oz = z0 + (w >> 2) + 2 * k;
+        const bool ok = ox < G.nx && oy < G.ny && oz < G.nz;
+        const long long pos = padded_pos(G, ox, oy, oz);
+        if (EPI == E_GATE && ok) {
+            gq[k][0] = __ldg(reinterpret_cast<const uint4 *>(A.gate + pos * kCh));
+            gq[k][1] = __ldg(reinterpret_cast<const uint4 *>(A.gate + pos * kCh + 8));
+        } else {
+            gq[k][0] = gq[k][1] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    cp_async_wait_all();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged data -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    // a thread's tcgen05.mma issue takes ~165 cycles however small the MMA,
+    // against ~10 cycles of tensor work at N = 16: lane 0 of warps 0-3 issue
+    // the 27 taps of one z-plane each, into their own TMEM columns
+    if (lane == 0 && w < kTZ) {
+        const int pl = w;
+        const uint32_t in_base = smem_u32(sm), w_base = smem_u32(sw);
+#pragma unroll 1
+        for (int t = 0; t < kTaps; ++t) {
+            const int s0 = (1 + tap_dx(t)) + kTSX * ((1 + tap_dy(t)) + kTSY * (1 + pl + tap_dz(t)));
+            const uint64_t ad = umma_desc(in_base + (uint32_t)s0 * 16, kTPlane, kTSX * 16);
+            const uint64_t bd = umma_desc(w_base + (uint32_t)t * 512, 256, 128);
+            umma_bf16(tmem + (uint32_t)pl * 16, ad, bd, kConvIdesc, t > 0 ? 1u : 0u);
+        }
+        umma_commit(bar);
+    }
+    bool done = mbar_wait_bounded(bar, 0, A.wait_ns);
+    tc_fence_after();
+    if (done) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int pl = (w >> 2) + 2 * k;
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)pl * 16, v);
+            const int oz = z0 + pl;
+            if (ox < G.nx && oy < G.ny && oz < G.nz) {
+                const long long pos = padded_pos(G, ox, oy, oz);
+                uint32_t o[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float a0 = __uint_as_float(v[2 * j]), a1 = __uint_as_float(v[2 * j + 1]);
+                    if (EPI == E_GATE) {
+                        const uint32_t gw = (&gq[k][j >> 2].x)[j & 3];
+                        const float2 g = unpack_bf16(gw);
+                        a0 *= g.x;
+                        a1 *= g.y;
+                    }
+                    o[j] = pack_bf16(a0, a1);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(A.out + pos * kCh);
+                dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+                dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            }
+        }
+    } else {
+        // report, then give the MMAs in flight a second bounded wait before
+        // the columns are freed
+        if (threadIdx.x == 0) {
+            if (A.st) finish(A.st, CG_ETIMEOUT);
+            if (A.err) atomicExch(A.err, CG_ETIMEOUT);
+        }
+        done = mbar_wait_bounded(bar, 0, A.wait_ns);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTCols) : "memory");
+    }
 }
 
 // --------------------------------------------------- 1 -> 16 convolution
@@ -1157,6 +1355,7 @@ struct LearnCtx {
     double *dsq = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     double *partials = nullptr, *sigma = nullptr;
     unsigned int *counter = nullptr;
+    int *conv_err = nullptr;         // timeout report of the tensor-core convolution (apply)
     FcgState *st = nullptr;
     DevStatus *dst = nullptr;
     FcgState *st_host = nullptr;     // pinned
@@ -1222,6 +1421,8 @@ int set_smem_limits() {
     set((const void *)conv16_kernel<E_GATE>);
     set((const void *)conv16_kernel<E_GATE_PRE>);
     set((const void *)conv16_kernel<E_BWD_GATE>);
+    set((const void *)conv16tc_kernel<E_STORE>);
+    set((const void *)conv16tc_kernel<E_GATE>);
     set((const void *)convout_kernel<E_OUT_U>);
     set((const void *)convout_kernel<E_OUT_Z>);
     set((const void *)convout_kernel<E_OUT_FCG>);
@@ -1244,6 +1445,7 @@ int set_smem_limits() {
 ConvArgs conv_args(const Geo &G) {
     ConvArgs A{};
     A.G = G;
+    A.wait_ns = 5000000000ull;
     return A;
 }
 
@@ -1299,12 +1501,13 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.in = L->h1;
     A.w = net->d.k2;
     A.out = L->h2;
-    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.wait_ns = (unsigned long long)(h->opts.wait_limit_s * 1e9);
+    conv16tc_kernel<E_STORE><<<G.ttiles, kCT, conv16tc_smem(G), s>>>(A);
     // k1 = g * C2^T(h2)
     A.in = L->h2;
     A.w = net->d.k2t;
     A.out = L->k1;
-    conv16_kernel<E_GATE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    conv16tc_kernel<E_GATE><<<G.ttiles, kCT, conv16tc_smem(G), s>>>(A);
     // z = sigma D^-1/2 C1^T(k1) (or D^-1 r), z.r, z.q, beta
     A.in = L->k1;
     A.w = net->d.k1t;
@@ -1747,7 +1950,7 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
         (rc = ctx_alloc(A, &L->z, (size_t)G.n)) || (rc = ctx_alloc(A, &L->p, (size_t)G.n + 16)) ||
         (rc = ctx_alloc(A, &L->q, (size_t)G.n)) || (rc = ctx_alloc(A, &L->partials, (size_t)3 * nparts)) ||
         (rc = ctx_alloc(A, &L->sigma, 4)) || (rc = ctx_alloc(A, &L->counter, 4)) || (rc = ctx_alloc(A, &L->st, 1)) ||
-        (rc = ctx_alloc(A, &L->dst, 1)))
+        (rc = ctx_alloc(A, &L->dst, 1)) || (rc = ctx_alloc(A, &L->conv_err, 1)))
         return fail(rc);
     if (cudaMallocHost(&L->st_host, sizeof(FcgState)) != cudaSuccess ||
         cudaMallocHost(&L->flags_host, 2 * sizeof(FcgFlags)) != cudaSuccess ||
@@ -1799,17 +2002,23 @@ int cg_precond_apply(cg_handle *h, const double *r, double *z) {
     A.in = L->h1;
     A.w = L->net->d.k2;
     A.out = L->h2;
-    conv16_kernel<E_STORE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    A.wait_ns = (unsigned long long)(h->opts.wait_limit_s * 1e9);
+    A.err = L->conv_err;
+    conv16tc_kernel<E_STORE><<<G.ttiles, kCT, conv16tc_smem(G), s>>>(A);
     A.in = L->h2;
     A.w = L->net->d.k2t;
     A.out = L->k1;
-    conv16_kernel<E_GATE><<<G.tiles, kCT, conv16_smem(G), s>>>(A);
+    conv16tc_kernel<E_GATE><<<G.ttiles, kCT, conv16tc_smem(G), s>>>(A);
     A.in = L->k1;
     A.w = L->net->d.k1t;
     A.z = z;
     convout_kernel<E_OUT_Z><<<G.tiles, kCT, convout_smem(G), s>>>(A);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return CG_ECUDA;
-    return CG_OK;
+    int err = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&err, L->conv_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CG_ECUDA;
+    return err ? err : CG_OK;
 }
 
 int cg_learn_pairs(cg_handle *h, const double *b, const double *xstar, int32_t segment, int32_t count,
