@@ -95,6 +95,7 @@ KERNEL_SOURCES = {
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
     "conv16_kernel": ["learn.cu"] + _COMMON,
+    "conv16tc_kernel": ["learn.cu"] + _COMMON,
     "convout_kernel": ["learn.cu"] + _COMMON,
     "conv1_kernel": ["learn.cu"] + _COMMON,
     "fcg_spmv_kernel": ["learn.cu", "plan.h"] + _COMMON,
