@@ -187,6 +187,22 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The largest `value` over the ranks of the default process group: the
+    job's time is its slowest replica's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_solve(total_ms: float, steps: int, world: int) -> float:
+    """Whole-job ms per solve: every rank solves `steps` systems in the
+    slowest rank's `total_ms`."""
+    return total_ms / (steps * world)
+
+
 def run_reference(args) -> None:
     """The oracle (serial C, FP64) on the same workload, on the host cores."""
     world, rank, _ = dist_setup()
@@ -642,11 +658,9 @@ def run_gbcg(args) -> None:
     relres_true = res[-1][1].relres_true
     launches = sum(i.launches for _, i in res)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / args.steps
-    value = total_ms / (args.steps * world)
+    value = job_ms_per_solve(total_ms, args.steps, world)
 
     bpi = bytes_per_iteration(n, nnz, False)
     fpi = flops_per_iteration(n, nnz, False)
