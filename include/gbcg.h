@@ -146,9 +146,12 @@ typedef struct {
     int32_t reg_rows;        /* rows per thread held in registers (0: none)       */
     int32_t window_tiles;    /* tiles whose gathers read a staged x-window        */
     int64_t device_bytes;    /* device memory the handle owns                     */
-    int32_t slice_solve;     /* 1: FP64 solves run the SELL-32 kernel (one 32-row
-                                slice per warp, 1024 threads per CTA); 0: the
-                                tiled kernel described by the fields above       */
+    int32_t slice_solve;     /* FP64 solves run: 1 the SELL-32 kernel with one
+                                32-row slice per warp and rows in registers; 2
+                                the SELL-32 kernel with the vectors in memory
+                                (systems too large for 1 and for register rows
+                                in the tiled kernel); 0 the tiled kernel
+                                described by the fields above                    */
     int32_t reserved;        /* 0                                                 */
 } cg_plan;
 

@@ -773,6 +773,214 @@ out:
     return;
 }
 
+// ------------------------------------------ the SELL-32 memory-mode solve
+// For systems with more slices than the slice kernel holds (n > 150,784 on
+// 152 SMs): the same CG iteration with the vectors in global memory.  The
+// vectors (x, r, p, q, the published z, 1/diag: 6 x 8 bytes per row) stay in
+// L2 while the matrix streams through it marked evict-first.  Warp w of CTA
+// c takes slices cut[c] + w, + 32, ... of the CTA's contiguous range (ranges
+// balanced by FP64 work on the host); a row is always read and written by
+// the same thread.  Two grid barriers per iteration; each decision is taken
+// before the next phase starts.
+template <bool PRE>
+__global__ void __launch_bounds__(kSellSolveThreads, 1)
+    cg_sellmem_kernel(Params P, SellMatrix M, const int32_t *__restrict__ cut) {
+    __shared__ double red[3 * kSellSolveThreads];
+    __shared__ double quarter[12];
+    __shared__ double bcast[8];
+    __shared__ int ctl[16];
+    Smem S{};
+    S.red = red;
+    S.bcast = bcast;
+    S.ctl = ctl;
+    unsigned int epoch = 0;
+    int set = 0;
+    constexpr int kW = kSellSolveThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int t0 = cut[blockIdx.x] + (tid >> 5), t1 = cut[blockIdx.x + 1];
+    double *const zg = P.p0;   // z: the vector the SpMV gathers
+    double *const pv = P.pd;   // p
+
+    // thread 0's scalar state
+    int status = CG_OK, iters = 0;
+    double rr = 0.0, bb = 0.0, true_rr = -1.0, rho = 0.0, bnorm = 0.0, tol2bb = 0.0;
+
+    // ---- setup: r0 = b - A x0, z0 = M^-1 r0, p0 = z0, q = 0; r.r, r.z, b.b
+    bool run;
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int t = t0; t < t1; t += kW) {
+            const double ax = sell_slice_sum(M, t, P.x, 0.0);
+            const int row = t * 32 + lane;
+            if (row < P.n) {
+                const double bi = P.b[row];
+                const double ri = bi - ax;
+                const double zi = PRE ? __ldg(P.dinv + row) * ri : ri;
+                P.r[row] = ri;
+                zg[row] = zi;
+                pv[row] = zi;
+                P.q[row] = 0.0;
+                v[0] = fma(ri, ri, v[0]);
+                v[1] = fma(ri, zi, v[1]);
+                v[2] = fma(bi, bi, v[2]);
+            }
+        }
+        block_sum_1k<3>(v, red, quarter);
+        publish_partials<3>(P, set, v);
+        if (!grid_barrier(P, epoch, S)) goto out;
+        double tot[3];
+        grid_totals_1k<3>(P, set, tot, quarter);
+        set ^= 1;
+        if (tid == 0) {
+            rr = tot[0];
+            bb = tot[2];
+            rho = tot[1];
+            bnorm = sqrt(bb);
+            tol2bb = (P.tol * bnorm) * (P.tol * bnorm);
+            int go = 0, zero_b = 0;
+            if (!finite_bits(bb)) {
+                status = CG_ENAN;
+            } else if (bnorm == 0.0) {
+                rr = 0.0;
+                zero_b = 1;
+            } else if (!finite_bits(rr) || !finite_bits(rho)) {
+                status = CG_ENAN;
+            } else if (rr <= tol2bb) {
+                status = CG_OK;
+            } else if (!(rho > 0.0)) {
+                status = CG_EBREAKDOWN;
+            } else {
+                go = 1;
+            }
+            ctl[kCtlRun] = go;
+            ctl[kCtlZeroB] = zero_b;
+        }
+        __syncthreads();
+        run = ctl[kCtlRun] != 0;
+        if (ctl[kCtlZeroB])   // b = 0: the solution is x = 0
+            for (int t = t0; t < t1; t += kW)
+                if (t * 32 + lane < P.n) P.x[t * 32 + lane] = 0.0;
+    }
+
+    // ---- the CG loop
+    if (run) {
+        if (tid == 0) status = CG_ENOCONV;
+        constexpr int NB = PRE ? 2 : 1;
+        double beta = 0.0;   // p_1 = z_0, q_1 = A z_0
+        for (int k = 1; k <= P.maxit; ++k) {
+            // phase A: q = A z + beta q (= A p), p = z + beta p; p . q
+            double v1[1] = {0.0};
+            for (int t = t0; t < t1; t += kW) {
+                const double az = sell_slice_sum(M, t, zg, 0.0);
+                const int row = t * 32 + lane;
+                if (row < P.n) {
+                    const double qi = fma(beta, P.q[row], az);
+                    const double pi = fma(beta, pv[row], zg[row]);
+                    P.q[row] = qi;
+                    pv[row] = pi;
+                    v1[0] = fma(pi, qi, v1[0]);
+                }
+            }
+            block_sum_1k<1>(v1, red, quarter);
+            publish_partials<1>(P, set, v1);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double sg[1];
+            grid_totals_1k<1>(P, set, sg, quarter);
+            set ^= 1;
+            if (tid == 0) {
+                const double sigma = sg[0];
+                int go = 0;
+                if (!finite_bits(sigma)) status = CG_ENAN;
+                else if (!(sigma > 0.0)) status = CG_EBREAKDOWN;
+                else go = 1;
+                bcast[0] = go ? rho / sigma : 0.0;
+                ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!ctl[kCtlRun]) break;
+            const double alpha = bcast[0];
+
+            // phase B: x += alpha p, r -= alpha q, z = dinv r (published); r.r, r.z
+            double v2[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) v2[j] = 0.0;
+            for (int t = t0; t < t1; t += kW) {
+                const int row = t * 32 + lane;
+                if (row < P.n) {
+                    const double ri = fma(-alpha, P.q[row], P.r[row]);
+                    P.x[row] = fma(alpha, pv[row], P.x[row]);
+                    P.r[row] = ri;
+                    const double zi = PRE ? __ldg(P.dinv + row) * ri : ri;
+                    zg[row] = zi;
+                    v2[0] = fma(ri, ri, v2[0]);
+                    if constexpr (PRE) v2[NB - 1] = fma(ri, zi, v2[NB - 1]);
+                }
+            }
+            block_sum_1k<NB>(v2, red, quarter);
+            publish_partials<NB>(P, set, v2);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double t2[NB];
+            grid_totals_1k<NB>(P, set, t2, quarter);
+            set ^= 1;
+            if (tid == 0) {
+                iters = k;
+                rr = t2[0];
+                const double rho_new = t2[NB - 1];
+                int go = 0;
+                if (!finite_bits(rr)) status = CG_ENAN;
+                else if (rr <= tol2bb) status = CG_OK;
+                else if (!finite_bits(rho_new)) status = CG_ENAN;
+                else if (!(rho_new > 0.0)) status = CG_EBREAKDOWN;
+                else if (k < P.maxit) go = 1;  // else ENOCONV
+                if (go) {
+                    bcast[1] = rho_new / rho;
+                    rho = rho_new;
+                }
+                ctl[kCtlRun] = go;
+            }
+            __syncthreads();
+            if (!ctl[kCtlRun]) break;
+            beta = bcast[1];
+        }
+    }
+
+    // ---- the true residual ||b - A x||
+    {
+        if (tid == 0) ctl[kCtlTrue] = (P.true_res && status != CG_ENAN && bb != 0.0) ? 1 : 0;
+        __syncthreads();
+        const bool want_true = ctl[kCtlTrue] != 0;
+        if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
+        if (want_true) {
+            if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
+            double v[1] = {0.0};
+            for (int t = t0; t < t1; t += kW) {
+                const double ax = sell_slice_sum(M, t, P.x, 0.0);
+                const int row = t * 32 + lane;
+                if (row < P.n) {
+                    const double d = P.b[row] - ax;
+                    v[0] = fma(d, d, v[0]);
+                }
+            }
+            block_sum_1k<1>(v, red, quarter);
+            publish_partials<1>(P, set, v);
+            if (!grid_barrier(P, epoch, S)) goto out;
+            double tt[1];
+            grid_totals_1k<1>(P, set, tt, quarter);
+            if (tid == 0) true_rr = tt[0];
+        }
+    }
+
+    if (blockIdx.x == 0 && tid == 0) {
+        P.st->iters = iters;
+        P.st->rr = rr;
+        P.st->bb = bb;
+        P.st->true_rr = true_rr;
+        atomicCAS(&P.st->status, 0, status);
+    }
+out:
+    return;
+}
+
 // ---------------------------------------------- mixed-precision solve
 // Iterative refinement: the outer loop keeps x and the residual in FP64 with
 // the FP64 matrix (r = b - A x, stop when ||r|| <= tol ||b||, x += d); each
@@ -1053,11 +1261,14 @@ int enqueue_solve(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev0, h->stream);
     if (e == cudaSuccess) {
-        if (h->sell_solve && h->opts.inner_values == CG_VALUES_FP64) {
+        if ((h->sell_solve || h->sell_mem) && h->opts.inner_values == CG_VALUES_FP64) {
             SellMatrix M = sell_of(h);
             const int32_t *cut = h->sell_cut;
             void *args[] = {&P, &M, &cut};
-            const void *kern = precond ? (const void *)cg_sell_kernel<true> : (const void *)cg_sell_kernel<false>;
+            const void *kern =
+                h->sell_solve ? (precond ? (const void *)cg_sell_kernel<true> : (const void *)cg_sell_kernel<false>)
+                              : (precond ? (const void *)cg_sellmem_kernel<true>
+                                         : (const void *)cg_sellmem_kernel<false>);
             e = cudaLaunchCooperativeKernel(kern, dim3(h->ctas), dim3(kSellSolveThreads), args, 0, h->stream);
         } else {
             void *args[] = {&P};
@@ -1381,6 +1592,31 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
                 h->sell_solve = 1;
             }
         }
+        // larger systems (no register rows in the tiled kernel): the SELL-32
+        // kernel with the vectors in memory, slices in contiguous ranges per CTA
+        if (!h->sell_solve && !opts.vectors_in_memory && h->rpt == 0 && n > 0) {
+            const std::vector<int32_t> mcut = split_slices(sh.ptr, ctas, h->sell_slices, kSliceVecCost);
+            int occ_plain = 0, occ_pre = 0;
+            const bool ok =
+                !mcut.empty() &&
+                cudaFuncSetAttribute((const void *)cg_sellmem_kernel<false>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxL1) == cudaSuccess &&
+                cudaFuncSetAttribute((const void *)cg_sellmem_kernel<true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxL1) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, cg_sellmem_kernel<false>,
+                                                              kSellSolveThreads, 0) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pre, cg_sellmem_kernel<true>,
+                                                              kSellSolveThreads, 0) == cudaSuccess;
+            if (ok && occ_plain >= 1 && occ_pre >= 1) {
+                if ((rc = dev_alloc(h, &h->sell_cut, mcut.size()))) return fail(rc);
+                if (cudaMemcpy(h->sell_cut, mcut.data(), sizeof(int32_t) * mcut.size(), cudaMemcpyHostToDevice) !=
+                    cudaSuccess)
+                    return fail(CG_ECUDA);
+                h->sell_mem = 1;
+            }
+        }
         const size_t tot = sh.vals.size();
         if ((rc = dev_alloc(h, &h->sell_ptr, sh.ptr.size())) || (rc = dev_alloc(h, &h->sell_vals, tot)))
             return fail(rc);
@@ -1519,7 +1755,7 @@ int cg_get_plan(const cg_handle *h, cg_plan *plan) {
     p.reg_rows = h->rpt;
     p.window_tiles = h->window_tiles;
     p.device_bytes = h->device_bytes;
-    p.slice_solve = h->sell_solve;
+    p.slice_solve = h->sell_solve ? 1 : (h->sell_mem ? 2 : 0);
     *plan = p;
     return CG_OK;
 }

@@ -58,6 +58,7 @@ struct cg_handle {
     int32_t sell_slices = 0;
     int sell_grid = 0;                // CTAs of a SELL SpMV launch
     int sell_solve = 0;               // 1: FP64 solves run cg_sell_kernel
+    int sell_mem = 0;                 // 1: FP64 solves run cg_sellmem_kernel (vectors in memory)
     int32_t *sell_cut = nullptr;      // ctas + 1 slice boundaries of the slice kernel's CTAs
     int32_t *sell_split = nullptr;    // per slice: local block width (split layout), or nullptr
 };

@@ -173,16 +173,45 @@ def test_cg_paper_sized_full_solve(dev, precond, mem):
     assert rel(x, ref["x"]) <= 2.0 * rel(ref["x"], pr.xstar)
 
 
-def test_cg_large_fixed_k_and_full_solve(dev):
+@pytest.mark.parametrize("precond", [0, 1])
+def test_cg_large_fixed_k_and_full_solve(dev, precond):
     pr = problem("c3")
     k = 40
-    ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=k)
-    x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=k)
+    ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=k, precond=precond)
+    x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=k, precond=precond)
     assert info.iters == k and rel(x, ref["x"]) <= 1e-10
-    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol)
+    assert abs(info.relres - ref["relres"]) <= 1e-6 * ref["relres"]
+    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, precond=precond)
     assert info.status == gbcg.CG_OK and info.relres_true <= 1.05 * pr.tol
     true = np.linalg.norm(pr.b - oracle.spmv(pr.A, x)) / np.linalg.norm(pr.b)
     assert true <= 1.05 * pr.tol
+
+
+def test_memory_mode_sell_kernel_small(dev):
+    """On 2 CTAs the 20^3 box (290 slices) is too large for the slice kernel
+    and for register rows, so its solves run the SELL-32 kernel with the
+    vectors in memory: iterates, a full solve and the edge cases."""
+    pr = problem("c1")
+    kw = dict(grid_ctas=2)
+    with gbcg.Solver(pr.A, **kw) as s:
+        assert s.plan()["slice_solve"] == 2 and s.plan()["ctas"] == 2
+    for precond in (0, 1):
+        ref = oracle.cg(pr.A, pr.b, tol=0.0, maxit=60, precond=precond)
+        x, info = gpu_solve(pr.A, pr.b, dev, 0.0, maxit=60, precond=precond, **kw)
+        assert info.status == gbcg.CG_ENOCONV and info.iters == 60
+        assert rel(x, ref["x"]) <= 1e-10
+    ref = oracle_full("c1")
+    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, **kw)
+    assert info.status == gbcg.CG_OK and abs(info.iters - ref["iters"]) <= 2
+    assert rel(x, ref["x"]) <= 1e-10 and info.relres_true <= 1.01 * pr.tol
+    x, info = gpu_solve(pr.A, np.zeros(pr.A.n), dev, 1e-8, x0=np.ones(pr.A.n), **kw)
+    assert info.status == gbcg.CG_OK and info.iters == 0 and np.all(x == 0)
+    x0 = ref["x"] + 1e-3
+    r2 = oracle.cg(pr.A, pr.b, x0=x0, tol=pr.tol)
+    x, info = gpu_solve(pr.A, pr.b, dev, pr.tol, x0=x0, **kw)
+    assert abs(info.iters - r2["iters"]) <= 2 and rel(x, r2["x"]) <= 1e-10
+    x, info = gpu_solve(pr.A, pr.b, dev, 1e-10, wait_limit_s=2e-3, debug_phantom_arrivals=1, **kw)
+    assert info.status == gbcg.CG_ETIMEOUT
 
 
 @pytest.mark.parametrize("precond", [0, 1])
@@ -325,7 +354,7 @@ def test_device_resident_csr_input(dev):
 def test_plan_and_vector_modes(dev):
     with gbcg.Solver(problem("c3").A) as s:
         assert s.plan()["reg_rows"] == 0          # too many rows per thread
-        assert s.plan()["slice_solve"] == 0       # more than one slice per warp
+        assert s.plan()["slice_solve"] == 2       # SELL-32 with the vectors in memory
     with gbcg.Solver(problem("c2").A, vectors_in_memory=True) as s:
         assert s.plan()["reg_rows"] == 0 and s.plan()["slice_solve"] == 0
     with gbcg.Solver(problem("c55").A) as s:
