@@ -91,6 +91,7 @@ _COMMON = ["cg_device.cuh", "layout.h"]
 KERNEL_SOURCES = {
     "cg_solve_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
     "cg_sell_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
+    "cg_sellmem_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
     "sell_spmv_kernel": ["gbcg.cu", "sell.cuh", "plan.h"],
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
@@ -507,6 +508,16 @@ def measure_forms_100cube(flush, count: int = 2) -> dict:
         info_v = res_v[-1][1]
         if name == "fp64_cg":
             x_fp64, ms_fp64 = xv.copy(), v_ms
+            # FP64-ALU roofline of the solve kernel (Table I's flop count)
+            kern = "cg_sellmem_kernel" if vs.plan()["slice_solve"] == 2 else "cg_solve_kernel"
+            kern_s = statistics.mean(i.kernel_ms for _, i in res_v) / 1e3
+            flops = info_v.iters * flops_per_iteration(big.A.n, big.A.nnz, False)
+            tr = ncu_traffic(kern)
+            out["roofline"] = {"bound": "alu", "kernel": kern, "achieved": round(flops / kern_s / 1e12, 4),
+                               "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                               "frac": round(flops / kern_s / 1e12 / FP64_PEAK_TFLOPS, 4),
+                               "traffic": (round(tr["dram_bytes_per_launch"]) if tr else None),
+                               "algorithmic_flops_per_launch": flops}
         out[name] = {"ms_per_solve": round(v_ms, 3), "iters": info_v.iters, "outer": info_v.outer,
                      "relres_true": info_v.relres_true,
                      "err_vs_fp64_cg": float(np.linalg.norm(xv - x_fp64) / np.linalg.norm(x_fp64)),
