@@ -61,6 +61,8 @@ struct cg_handle {
     int sell_mem = 0;                 // 1: FP64 solves run cg_sellmem_kernel (vectors in memory)
     int32_t *sell_cut = nullptr;      // ctas + 1 slice boundaries of the slice kernel's CTAs
     int32_t *sell_split = nullptr;    // per slice: local block width (split layout), or nullptr
+    void *sell_lo = nullptr;          // low-precision off-diagonals in the SELL layout (float or
+                                      // BF16 bits, per opts.inner_values), or nullptr
 };
 
 namespace gbcg {

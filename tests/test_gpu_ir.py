@@ -69,6 +69,21 @@ def test_refinement_reaches_fp64_accuracy(dev, name, values, precond):
     assert np.linalg.norm(x - ref["x"]) <= (r_gpu + r_ref) / lam_lb
 
 
+@pytest.mark.parametrize("values", [gbcg.CG_VALUES_FP32, gbcg.CG_VALUES_BF16], ids=["fp32", "bf16"])
+def test_refinement_tiled_kernel(dev, values):
+    """vectors_in_memory selects the tiled refinement kernel (the default
+    handles run the SELL-32 one): same accuracy bar on the 50^3 system."""
+    pr = problem("c2")
+    x, info = solve(pr.A, pr.b, dev, pr.tol, values, 1, vectors_in_memory=True)
+    assert info.status == gbcg.CG_OK and info.outer >= 2
+    assert info.relres_true <= pr.tol and true_relres(pr.A, pr.b, x) <= 1.05 * pr.tol
+    ref = oracle.cg(pr.A, pr.b, tol=pr.tol, precond=1)
+    lam_lb = 1e-2 * pr.mass.min()
+    r_gpu = np.linalg.norm(pr.b - oracle.spmv(pr.A, x))
+    r_ref = np.linalg.norm(pr.b - oracle.spmv(pr.A, ref["x"]))
+    assert np.linalg.norm(x - ref["x"]) <= (r_gpu + r_ref) / lam_lb
+
+
 @pytest.mark.parametrize("values,fmt", [(gbcg.CG_VALUES_FP32, oracle.FP32_FORMAT),
                                         (gbcg.CG_VALUES_BF16, oracle.BF16_FORMAT)], ids=["fp32", "bf16"])
 def test_refinement_steps_match_oracle(dev, values, fmt):
