@@ -517,7 +517,10 @@ __device__ __forceinline__ void grid_totals_1k(const Params &P, int set, double 
 // (L1-cached: the acquire fence of every grid barrier drops stale L1 lines),
 // never the read-only path; the matrix goes through L2 only, leaving L1 to
 // the gathered window of x.
-// Entries k0 <= k < k1 of the slice (k1 < 0: to the slice width).
+// Entries k0 <= k < k1 of the slice (k1 < 0: to the slice width), in
+// batches of U entries (all loads of a batch in flight before its FMAs),
+// then of kSellUnroll, then one at a time.
+template <int U = kSellUnroll>
 __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init,
                                                  int k0 = 0, int k1 = -1) {
     const int lane = threadIdx.x & 31;
@@ -530,6 +533,18 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
     int k = k0;
     if (M.cols16) {
         const int16_t *cc = M.cols16 + a + lane;
+        if constexpr (U != kSellUnroll) {
+            for (; k + U <= w; k += U) {
+                double vr[U], xr[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    vr[u] = mload(vv + (k + u) * 32, st);
+                    xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) s = fma(vr[u], xr[u], s);
+            }
+        }
         for (; k + kSellUnroll <= w; k += kSellUnroll) {
             double vr[kSellUnroll], xr[kSellUnroll];
 #pragma unroll
@@ -543,6 +558,18 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
         for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s);
     } else {
         const int32_t *cc = M.cols32 + a + lane;
+        if constexpr (U != kSellUnroll) {
+            for (; k + U <= w; k += U) {
+                double vr[U], xr[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    vr[u] = mload(vv + (k + u) * 32, st);
+                    xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) s = fma(vr[u], xr[u], s);
+            }
+        }
         for (; k + kSellUnroll <= w; k += kSellUnroll) {
             double vr[kSellUnroll], xr[kSellUnroll];
 #pragma unroll
@@ -782,6 +809,8 @@ out:
 // balanced by FP64 work on the host); a row is always read and written by
 // the same thread.  Two grid barriers per iteration; each decision is taken
 // before the next phase starts.
+constexpr int kSellUnrollMem = 18;   // no per-row registers here: deeper batches
+
 template <bool PRE>
 __global__ void __launch_bounds__(kSellSolveThreads, 1)
     cg_sellmem_kernel(Params P, SellMatrix M, const int32_t *__restrict__ cut) {
@@ -810,7 +839,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     {
         double v[3] = {0.0, 0.0, 0.0};
         for (int t = t0; t < t1; t += kW) {
-            const double ax = sell_slice_sum(M, t, P.x, 0.0);
+            const double ax = sell_slice_sum<kSellUnrollMem>(M, t, P.x, 0.0);
             const int row = t * 32 + lane;
             if (row < P.n) {
                 const double bi = P.b[row];
@@ -871,7 +900,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             // phase A: q = A z + beta q (= A p), p = z + beta p; p . q
             double v1[1] = {0.0};
             for (int t = t0; t < t1; t += kW) {
-                const double az = sell_slice_sum(M, t, zg, 0.0);
+                const double az = sell_slice_sum<kSellUnrollMem>(M, t, zg, 0.0);
                 const int row = t * 32 + lane;
                 if (row < P.n) {
                     const double qi = fma(beta, P.q[row], az);
@@ -954,7 +983,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
             double v[1] = {0.0};
             for (int t = t0; t < t1; t += kW) {
-                const double ax = sell_slice_sum(M, t, P.x, 0.0);
+                const double ax = sell_slice_sum<kSellUnrollMem>(M, t, P.x, 0.0);
                 const int row = t * 32 + lane;
                 if (row < P.n) {
                     const double d = P.b[row] - ax;
