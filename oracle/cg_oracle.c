@@ -27,7 +27,7 @@
  *         beta  = (r.z) / rho,  rho = r.z
  *         p     = z + beta p
  *
- * Readings where the paper is silent (each listed in the design doc):
+ * Readings where the paper is silent:
  *   - the stop test is the recursive residual 2-norm relative to ||b||_2
  *     (Table I gives only "tol=1e-10");
  *   - the iteration count is the number of products A p inside the loop;

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path (through the C ABI) against the CPU FP64 oracle.
 
-Tolerances (derived in DESIGN.md, "Parity bars"):
+Tolerances (derived from the arithmetic of each check):
   * SpMV, per row: |y - y_ref| <= 2 (m + 2) u sum_j |a_ij x_j|, m the row
     length, u = 2^-53 (the bound for two different summation orders of m terms).
   * CG iterates at a fixed iteration count k before the loss of orthogonality
