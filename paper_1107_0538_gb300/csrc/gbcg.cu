@@ -729,13 +729,12 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             if (!ctl[kCtlRun]) break;
             const double alpha = bcast[0];
 
-            // phase B: x += alpha p, r -= alpha q, z = dinv r (published); r.r, r.z
-            // (plain CG: z = r and r.z = r.r, one sum)
+            // phase B: r -= alpha q, z = dinv r (published); r.r, r.z (plain
+            // CG: z = r and r.z = r.r, one sum); x += alpha p below
             double v2[NB];
 #pragma unroll
             for (int j = 0; j < NB; ++j) v2[j] = 0.0;
             if (own) {
-                x = fma(alpha, p, x);
                 r = fma(-alpha, q, r);
                 z = PRE ? __ldg(dinv_g + row) * r : r;
                 zg[row] = z;
@@ -748,8 +747,14 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             // entries in this CTA's own rows (z written before grid_arrive's
             // __syncthreads) while thread 0 waits for the other CTAs
             grid_arrive(P, epoch);
-            if (has_slice) azl = sell_slice_sum(M, t, zg, 0.0, 0, wl);
-            else if (tid == 0) ctl[15] = grid_wait(P, epoch);
+            if (has_slice) {
+                // x is read by nothing before the end: x += alpha p leaves
+                // the critical path (p changes only in the next phase A)
+                if (own) x = fma(alpha, p, x);
+                azl = sell_slice_sum(M, t, zg, 0.0, 0, wl);
+            } else if (tid == 0) {
+                ctl[15] = grid_wait(P, epoch);
+            }
             __syncthreads();
             if (!ctl[15]) goto out;
             set ^= 1;   // this exchange's partials are set ^ 1 from here on
