@@ -152,7 +152,10 @@ typedef struct {
                                 (systems too large for 1 and for register rows
                                 in the tiled kernel); 0 the tiled kernel
                                 described by the fields above                    */
-    int32_t reserved;        /* 0                                                 */
+    int32_t inner_solve;     /* handles with inner_values FP32/BF16: 1 when the
+                                refinement runs on SELL-32 copies (one 32-row
+                                slice per warp), 0 when it runs on the staged
+                                tiles described above; 0 for FP64 handles       */
 } cg_plan;
 
 typedef struct cg_handle cg_handle;
@@ -206,6 +209,22 @@ int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t 
  */
 int cg_spmv(cg_handle *h, const double *x, double *y);
 
+/*
+ * y = A_lo x: the SpMV of the inner CG of iterative refinement alone (the
+ * "DGEMV(sparse)" of Section IV on the low-precision copy of A), for a handle
+ * created with inner_values FP32 or BF16.  A_lo is the matrix the inner solve
+ * uses: off-diagonals rounded (nearest-even) to FP32 or BF16, diagonal the
+ * FP32 row-sum compensated value (see cg_opts.inner_values).  x and y are
+ * device arrays of n floats; products and sums are FP32, each row's
+ * off-diagonal sum first, then y_i = fmaf(diag_i, x_i, sum), through the same
+ * device routine and launch layout as the handle's refinement kernel
+ * (cg_plan.inner_solve).  x is copied into the handle's workspace first, so
+ * this call must not overlap a solve on the same handle.  Synchronous.
+ * Returns CG_OK, CG_EINVAL (NULL handle or vectors, an FP64 handle),
+ * CG_ECUDA, or CG_ETIMEOUT if a bounded copy wait ran out.
+ */
+int cg_spmv_inner(cg_handle *h, const float *x, float *y);
+
 /* Fills *plan with the handle's launch plan.  CG_EINVAL on NULL arguments. */
 int cg_get_plan(const cg_handle *h, cg_plan *plan);
 
@@ -215,6 +234,19 @@ void cg_destroy(cg_handle *h);
 
 /* Static description of a status code ("unknown status" for other values). */
 const char *cg_strerror(int code);
+
+/*
+ * Measurement helper, not part of the method: the FP64 FMA throughput of the
+ * current device, the denominator of the FP64 roofline the solve kernels are
+ * reported against (one CG iteration is 2 NNZ + 10 N flops, Table I).  One
+ * kernel of 4 x SMs CTAs x 512 threads, each thread `iters` steps of 8
+ * independent FP64 FMA chains, timed with CUDA events on `stream` after a
+ * shorter warm-up launch.  *flops receives the flops of the timed launch
+ * (2 per FMA) and *ms its device time.  Writes no memory, allocates none.
+ * Synchronous.  CG_EINVAL for iters < 1 or NULL outputs, CG_ECUDA otherwise
+ * on failure.
+ */
+int cg_fp64_peak(void *stream, int32_t iters, double *flops, double *ms);
 
 /* ---- batched solves ---------------------------------------------------- */
 
@@ -299,24 +331,29 @@ void cg_batch_destroy(cg_batch *h);
 #define CG_NOALLOC_MAX_N 262144
 
 /*
- * FP64 CG without any allocation, for callers that cannot allocate: code
- * running while a stream is captured into a graph (cudaMalloc is not a
- * capturable operation and synchronizes the device), code inside a framework
- * whose caching allocator owns all device memory, real-time loops that cannot
- * afford an allocation's synchronization.  The paper has no counterpart; it
- * computes what cg_solve computes with CG_PRECOND_NONE (same recurrence, stop
- * test and status codes) from the caller's arrays: A must be CG_MEM_DEVICE
- * (rowptr, colidx, vals on the current device), b and x are device vectors
+ * FP64 CG without any allocation, for callers that cannot allocate device
+ * memory: code inside a framework whose caching allocator owns the device
+ * memory (a cudaMalloc beside it can fail, and it synchronizes the device),
+ * real-time loops with no room for that synchronization, plug-ins with a
+ * fixed device-memory budget.  The paper has no counterpart; it computes
+ * what cg_solve computes with CG_PRECOND_NONE (same recurrence, stop test
+ * and status codes) from the caller's arrays: A must be CG_MEM_DEVICE with
+ * rowptr, colidx and vals on the current device, b and x are device vectors
  * (x: in x0, out the last iterate), stream is a cudaStream_t.  Its workspace
  * is one fixed __device__ array shared by all calls: each call clears what
  * must start at zero, but calls whose work overlaps on the GPU (other
  * streams, other host threads) race on it.  The first call on a device looks
- * the array's address up (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Synchronous.  Returns CG_EINVAL for n >
- * CG_NOALLOC_MAX_N, host-resident arrays, NULL vectors or b == x, and for a
- * malformed matrix found by the kernel (row range or column out of bounds;
- * such entries are never read); otherwise as cg_solve.  info->kernel_ms is 0
- * and relres_true is -1 (no events, no extra SpMV).
+ * the array's address up (cudaGetSymbolAddress) and, under lazy module
+ * loading, loads the module that holds the array (it is created then); make
+ * that first call before any stream capture.  cudaDeviceReset invalidates the
+ * looked-up address: do not call this again on a device that was reset.
+ * Synchronous: returns once the result and the status are back.  Returns
+ * CG_EINVAL for n > CG_NOALLOC_MAX_N, NULL vectors, b == x, any array that is
+ * not device or managed memory of the current device (checked on the host
+ * with cudaPointerGetAttributes before any launch), and for a malformed
+ * matrix found by the kernel (a row range or a column out of bounds; such
+ * entries are never read); otherwise as cg_solve.  info->kernel_ms is 0 and
+ * relres_true is -1 (no events, no extra SpMV).
  */
 int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit,
                      void *stream, cg_info *info);

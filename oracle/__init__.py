@@ -14,6 +14,11 @@ Parity status of each function (what pins it is in ``tests/test_oracle.py``):
   spmv, cg (plain and Jacobi), round_to_format  -- pinned
   lowprec_values                                -- pinned (row sums, SPD, format)
   cg_ir                                         -- pinned (reduces to CG; exact-solve limit)
+
+``cg_omp`` (``cg_omp.c``, built with OpenMP) is not part of the oracle: it is
+the multi-core CPU baseline that ``bench.py`` times on all host cores.  It
+sums its dot products per thread, so its rounding differs from ``cg``; its
+test checks it against ``cg``.
 """
 from __future__ import annotations
 
@@ -27,8 +32,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cg_oracle.c")
 _SO = os.path.join(_HERE, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "cg_omp.c")
+_OMP_SO = os.path.join(_HERE, "libcg_omp.so")
 _LOCK = threading.Lock()
 _LIB = None
+_OMP = None
 
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENAN = 0, 1, 2, 4, 5, 6
 STATUS_NAMES = {OK: "ok", EINVAL: "einval", ENOMEM: "enomem", ENOCONV: "enoconv",
@@ -40,15 +48,54 @@ BF16_FORMAT = (8, -126, 127)
 
 
 def build(force: bool = False) -> str:
-    """Compile cg_oracle.c into liboracle.so next to it (gcc, no FMA contraction)."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
+    """Compile cg_oracle.c into liboracle.so next to it (gcc, no FMA contraction),
+    and the OpenMP baseline cg_omp.c into libcg_omp.so."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    if force or not os.path.exists(_OMP_SO) or os.path.getmtime(_OMP_SO) < os.path.getmtime(_OMP_SRC):
+        tmp = _OMP_SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _OMP_SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OMP_SO)
     return _SO
+
+
+def _omp():
+    global _OMP
+    with _LOCK:
+        if _OMP is None:
+            build()
+            lib = ctypes.CDLL(_OMP_SO)
+            i32, dbl, vp = ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+            lib.cpu_cg_omp.argtypes = [i32, vp, vp, vp, vp, vp, dbl, i32, ctypes.POINTER(i32),
+                                       ctypes.POINTER(dbl)]
+            lib.cpu_cg_omp.restype = ctypes.c_int
+            lib.cpu_omp_threads.argtypes = []
+            lib.cpu_omp_threads.restype = ctypes.c_int
+            _OMP = lib
+    return _OMP
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP baseline runs with (OMP_NUM_THREADS, else all host cores)."""
+    return int(_omp().cpu_omp_threads())
+
+
+def cg_omp(A, b, x0=None, tol: float = 1e-8, maxit: int = 0) -> dict:
+    """Plain FP64 CG with OpenMP row and vector loops: the timed multi-core CPU
+    baseline, not the parity reference.  Returns dict(x, iters, relres, status)."""
+    n, rowptr, colidx, vals = _csr_arrays(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = _omp().cpu_cg_omp(n, _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(b), _ptr(x), float(tol),
+                           int(maxit), ctypes.byref(it), ctypes.byref(rel))
+    return dict(x=x, iters=int(it.value), relres=float(rel.value), status=int(st))
 
 
 def _lib():

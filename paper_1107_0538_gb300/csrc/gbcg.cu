@@ -1447,6 +1447,69 @@ __global__ void __launch_bounds__(kSellThreads) sell_spmv_kernel(SellMatrix M, c
     sell_rows(M, x, epi);
 }
 
+// ------------------------------------------ the inner SpMV on its own
+// y = A_lo x with the low-precision inner matrix, through the very device
+// routines the refinement kernels run in their inner CG (the staged tiles of
+// cg_ir_kernel, or the SELL-32 slices of cg_irsell_kernel with the same
+// CTA/warp/slice mapping), so that the inner product can be checked entry by
+// entry.  x is the handle's padded inner vector p32 (the window source);
+// y_i = fmaf(diag_lo_i, x_i, off-diagonal sum), as in the inner iteration.
+struct EpiLoStore {
+    float *y;
+    const float *x;
+    const float *diag;
+    __device__ __forceinline__ void row(int i, float s, int) { y[i] = fmaf(diag[i], x[i], s); }
+};
+
+template <class VT>
+__global__ void __launch_bounds__(kThreads, 1) lo_spmv_tiles_kernel(Params P, float *y) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Smem S = carve_smem(smem_raw);
+    init_pipeline(S);
+    Pipe pipe;
+    const VT *vlo = nullptr;
+    if constexpr (sizeof(VT) == 4) vlo = reinterpret_cast<const VT *>(P.vals32);
+    else vlo = reinterpret_cast<const VT *>(P.vals16);
+    EpiLoStore epi{y, P.p32, P.diag_lo};
+    spmv_tiles<0, VT, float, float>(P, S, pipe, vlo, P.p32, epi, true);
+    drain<float, float>(P, S, pipe, P.p32);
+}
+
+template <class VT>
+__global__ void __launch_bounds__(kSellSolveThreads, 1)
+    lo_spmv_sell_kernel(Params P, SellMatrix M, const VT *__restrict__ vlo, const int32_t *__restrict__ cut,
+                        float *y) {
+    constexpr int kW = kSellSolveThreads / 32;
+    const int lane = threadIdx.x & 31;
+    const int t0 = cut[blockIdx.x] + (threadIdx.x >> 5), t1 = cut[blockIdx.x + 1];
+    for (int t = t0; t < t1; t += kW) {
+        const float s = sell_slice_sum_lo<VT>(M, vlo, t, P.p32);
+        const int row = t * 32 + lane;
+        if (row < P.n) y[row] = fmaf(__ldg(P.diag_lo + row), P.p32[row], s);
+    }
+}
+
+// ---------------------------------------------- FP64 throughput probe
+// The FP64 roofline's denominator, measured: every thread runs 8 independent
+// FMA chains (enough to cover the dependent-FMA latency with 16 warps per
+// SM sub-partition), 2 flops per FMA.  The result is stored only if it takes
+// an impossible value, so the chains stay live and nothing is written.
+__device__ double g_fp64_probe_sink;
+
+__global__ void __launch_bounds__(512) fp64_fma_probe_kernel(int iters, double seed) {
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + 1e-9 * (double)(threadIdx.x + 64 * j);
+    const double m = 0.9999999999, c = 1e-12;
+#pragma unroll 4
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+    }
+    const double s = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    if (s == -12345.0) g_fp64_probe_sink = s;
+}
+
 constexpr int kRptChoices[] = {0, 1, 2, 4};
 SolveKernel solve_kernel_for(int rpt) {
     switch (rpt) {
@@ -1754,6 +1817,10 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
         cudaFuncSetAttribute((const void *)cg_ir_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kSmemBytes) != cudaSuccess ||
         cudaFuncSetAttribute((const void *)cg_ir_kernel<__nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)lo_spmv_tiles_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)lo_spmv_tiles_kernel<__nv_bfloat16>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess)
         return fail(CG_ECUDA);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(4), kThreads, kSmemBytes) !=
@@ -2068,6 +2135,39 @@ int cg_spmv(cg_handle *h, const double *x, double *y) {
     return enqueue_spmv(h, x, y);
 }
 
+int cg_spmv_inner(cg_handle *h, const float *x, float *y) {
+    if (!h || h->opts.inner_values == CG_VALUES_FP64) return CG_EINVAL;
+    if (h->n == 0) return CG_OK;
+    if (!x || !y) return CG_EINVAL;
+    DeviceGuard g(h->device);
+    // the inner kernels gather from the handle's padded, 16-byte aligned p32
+    cudaError_t e = cudaMemcpyAsync(h->p32, x, sizeof(float) * (size_t)h->n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->st, 0, sizeof(DevStatus), h->stream);
+    if (e == cudaSuccess) {
+        Params P = base_params(h);
+        const bool fp32 = h->opts.inner_values == CG_VALUES_FP32;
+        if (h->sell_lo) {
+            const SellMatrix M = sell_of(h);
+            if (fp32)
+                lo_spmv_sell_kernel<float><<<h->ctas, kSellSolveThreads, 0, h->stream>>>(
+                    P, M, static_cast<const float *>(h->sell_lo), h->sell_cut, y);
+            else
+                lo_spmv_sell_kernel<__nv_bfloat16><<<h->ctas, kSellSolveThreads, 0, h->stream>>>(
+                    P, M, static_cast<const __nv_bfloat16 *>(h->sell_lo), h->sell_cut, y);
+        } else if (fp32) {
+            lo_spmv_tiles_kernel<float><<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P, y);
+        } else {
+            lo_spmv_tiles_kernel<__nv_bfloat16><<<h->ctas, kThreads, kSmemBytes, h->stream>>>(P, y);
+        }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->st_host, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return CG_ECUDA;
+    return h->st_host->status;   // CG_OK, or CG_ETIMEOUT if a TMA wait ran out
+}
+
 int cg_get_plan(const cg_handle *h, cg_plan *plan) {
     if (!h || !plan) return CG_EINVAL;
     cg_plan p{};
@@ -2085,10 +2185,37 @@ int cg_get_plan(const cg_handle *h, cg_plan *plan) {
     p.window_tiles = h->window_tiles;
     p.device_bytes = h->device_bytes;
     p.slice_solve = h->sell_solve ? 1 : (h->sell_mem ? 2 : 0);
+    p.inner_solve = h->sell_lo ? 1 : 0;
     *plan = p;
     return CG_OK;
 }
 
 void cg_destroy(cg_handle *h) { free_handle(h); }
+
+int cg_fp64_peak(void *stream, int32_t iters, double *flops, double *ms) {
+    if (iters < 1 || !flops || !ms) return CG_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CG_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks = sms * 4, threads = 512;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CG_ECUDA;
+    fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters / 8 + 1, 1.0);   // warm-up
+    cudaEventRecord(e0, st);
+    fp64_fma_probe_kernel<<<blocks, threads, 0, st>>>(iters, 1.0);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    float t = 0.0f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return CG_ECUDA;
+    *flops = 2.0 * 8.0 * (double)iters * (double)blocks * (double)threads;
+    *ms = (double)t;
+    return CG_OK;
+}
 
 }  // extern "C"

@@ -1,23 +1,34 @@
 // cg_solve_noalloc: the FP64 CG solve for callers that cannot allocate
 // device memory.
 //
-// Some callers of this library may not call cudaMalloc: code that runs while
-// a CUDA stream is being captured into a graph (allocation is not a
-// capturable operation and cudaMalloc synchronizes the device), code embedded
-// in a framework whose caching allocator owns all device memory, and
-// real-time loops that cannot afford the synchronization an allocation
-// implies.  cg_create allocates the matrix copy and the solver workspace, so
+// Some callers of this library may not call cudaMalloc: code embedded in a
+// framework whose caching allocator owns the device memory (a cudaMalloc
+// beside it can fail once the framework holds the memory, and it
+// synchronizes the whole device), real-time loops whose latency budget has no
+// room for the device-wide synchronization an allocation implies, and
+// plug-ins that run inside a host application with a fixed device-memory
+// budget.  cg_create allocates the matrix copy and the solver workspace, so
 // those callers cannot use it.  This entry point takes the matrix and the
 // vectors from the caller and keeps its workspace (three vectors, the
 // per-CTA partial sums, the grid-barrier counter and the status block) in one
 // file-scope __device__ array of fixed size, so it allocates nothing, on the
-// device or on the host.
+// device or on the host.  It is synchronous: it returns once the result and
+// the status are back.
 //
 // The workspace array is shared by every call in the process and keeps the
 // contents of the last call: each call clears what must start at zero (the
 // barrier counter and the status block) and writes every vector entry before
 // reading it.  Two calls whose work overlaps on the GPU (on different streams,
 // or from different host threads) race on that array.
+//
+// In host code the array's name only stands for it: its device address is
+// looked up with cudaGetSymbolAddress, once per device, with that device
+// current, on the device's first call.  With lazy module loading (the CUDA
+// default) that first call is also what loads this module on the device and
+// so creates the array; make it before any stream capture.  cudaDeviceReset
+// destroys the array with the context, so the cached address is stale after
+// it: a process that resets a device must not call this entry point on it
+// again.
 //
 // It is a variant of cg_solve_kernel: the same recurrence, fixed-order
 // reductions, thread-0 scalars and bounded grid barriers, with a plain
@@ -253,6 +264,20 @@ int noalloc_setup(int dev, unsigned char **scratch, int *grid) {
     return CG_OK;
 }
 
+// True when p points into memory the current device can read in a kernel:
+// a device allocation of that device, or managed memory.  Host memory
+// (pageable or pinned) and other devices' allocations are refused before any
+// launch.  cudaPointerGetAttributes allocates nothing.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the (non-sticky) error recorded for an unknown pointer
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit,
@@ -267,6 +292,9 @@ extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, dou
     if (!A->rowptr || !b || !x || b == x || (A->nnz > 0 && (!A->colidx || !A->vals))) return CG_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CG_ECUDA;
+    if (!on_device(A->rowptr, dev) || !on_device(b, dev) || !on_device(x, dev) ||
+        (A->nnz > 0 && (!on_device(A->colidx, dev) || !on_device(A->vals, dev))))
+        return CG_EINVAL;
     unsigned char *scratch = nullptr;
     int grid = 0;
     int rc = noalloc_setup(dev, &scratch, &grid);

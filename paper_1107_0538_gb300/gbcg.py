@@ -28,7 +28,8 @@ CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
-           "cg_spmv", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_solve_noalloc",
+           "cg_spmv", "cg_spmv_inner", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_fp64_peak",
+           "cg_solve_noalloc",
            "cg_batch_create", "cg_batch_enqueue", "cg_batch_results", "cg_batch_solve",
            "cg_batch_tune", "cg_batch_destroy", "cg_net_create", "cg_net_get_params",
            "cg_net_set_params", "cg_net_destroy", "cg_set_learned", "cg_precond_apply", "cg_learn_pairs",
@@ -73,7 +74,7 @@ class cg_plan(ctypes.Structure):
                 ("lanes_per_row", ctypes.c_int32), ("l2_evict_first", ctypes.c_int32),
                 ("reg_rows", ctypes.c_int32), ("window_tiles", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("slice_solve", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("inner_solve", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -121,12 +122,16 @@ def lib() -> ctypes.CDLL:
                 f.restype = ctypes.c_int
             L.cg_spmv.argtypes = [vp, vp, vp]
             L.cg_spmv.restype = ctypes.c_int
+            L.cg_spmv_inner.argtypes = [vp, vp, vp]
+            L.cg_spmv_inner.restype = ctypes.c_int
             L.cg_get_plan.argtypes = [vp, ctypes.POINTER(cg_plan)]
             L.cg_get_plan.restype = ctypes.c_int
             L.cg_destroy.argtypes = [vp]
             L.cg_destroy.restype = None
             L.cg_strerror.argtypes = [ctypes.c_int]
             L.cg_strerror.restype = ctypes.c_char_p
+            L.cg_fp64_peak.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+            L.cg_fp64_peak.restype = ctypes.c_int
             L.cg_solve_noalloc.argtypes = [ctypes.POINTER(cg_csr), vp, vp, dbl, i32, vp,
                                            ctypes.POINTER(cg_info)]
             L.cg_solve_noalloc.restype = ctypes.c_int
@@ -208,6 +213,10 @@ def cg_spmv(h: int, x_ptr: int, y_ptr: int) -> int:
     return lib().cg_spmv(ctypes.c_void_p(h), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr))
 
 
+def cg_spmv_inner(h: int, x_ptr: int, y_ptr: int) -> int:
+    return lib().cg_spmv_inner(ctypes.c_void_p(h), ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr))
+
+
 def cg_get_plan(h: int) -> cg_plan:
     p = cg_plan()
     rc = lib().cg_get_plan(ctypes.c_void_p(h), ctypes.byref(p))
@@ -222,6 +231,14 @@ def cg_destroy(h: int | None) -> None:
 
 def cg_strerror(code: int) -> str:
     return lib().cg_strerror(int(code)).decode()
+
+
+def cg_fp64_peak(stream: int | None, iters: int) -> tuple[int, float, float]:
+    """(status, flops, ms) of the FP64 FMA throughput probe on the current device."""
+    flops = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    rc = lib().cg_fp64_peak(ctypes.c_void_p(stream or 0), int(iters), ctypes.byref(flops), ctypes.byref(ms))
+    return rc, flops.value, ms.value
 
 
 def cg_solve_noalloc(A: cg_csr, b_ptr: int, x_ptr: int, tol: float, maxit: int,
@@ -296,6 +313,12 @@ class Solver:
         if rc != CG_OK:
             raise GbcgError(rc, "cg_spmv")
 
+    def spmv_inner(self, x, y) -> None:
+        """y = A_lo x (float32 CUDA tensors) on a mixed-precision handle."""
+        rc = cg_spmv_inner(self.h, x.data_ptr(), y.data_ptr())
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_spmv_inner")
+
     def plan(self) -> dict:
         return cg_get_plan(self.h).as_dict()
 
@@ -364,7 +387,8 @@ class BatchSolver:
     tensors of shape (nrhs, N), N the total row count (systems concatenated)."""
 
     def __init__(self, systems, inner_values: int = CG_VALUES_FP32, precond: int = CG_PRECOND_NONE,
-                 inner_tol: float = 0.0, max_outer: int = 50, grid_ctas: int = 0, stream=None):
+                 inner_tol: float = 0.0, max_outer: int = 50, max_inner: int = 0, grid_ctas: int = 0,
+                 stream=None):
         import torch
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -373,6 +397,7 @@ class BatchSolver:
         o.precond = precond
         o.inner_tol = inner_tol
         o.max_outer = max_outer
+        o.max_inner = max_inner
         o.grid_ctas = grid_ctas
         arr = (cg_csr * len(systems))()
         self._keep = []

@@ -61,7 +61,7 @@ int main(void) {
   F(cg_plan, n) F(cg_plan, nnz) F(cg_plan, ctas) F(cg_plan, threads) F(cg_plan, tiles)
   F(cg_plan, tile_nnz) F(cg_plan, stages) F(cg_plan, smem_bytes) F(cg_plan, lanes_per_row)
   F(cg_plan, l2_evict_first) F(cg_plan, reg_rows) F(cg_plan, window_tiles) F(cg_plan, device_bytes)
-  F(cg_plan, slice_solve) F(cg_plan, reserved)
+  F(cg_plan, slice_solve) F(cg_plan, inner_solve)
   F(cg_batch_result, iters) F(cg_batch_result, outer) F(cg_batch_result, status) F(cg_batch_result, reserved)
   F(cg_batch_result, relres)
   F(cg_batch_tuning, inner_tol) F(cg_batch_tuning, gather_tiles) F(cg_batch_tuning, trials) F(cg_batch_tuning, best_ms)

@@ -345,3 +345,21 @@ def test_lowprec_values_rowsums_format_and_spd(fmt):
     if fmt == oracle.BF16_FORMAT:
         Dn = P.CSR(pr.A.n, pr.A.rowptr, pr.A.colidx, oracle.round_to_format(pr.A.vals, fmt)).to_dense()
         assert np.linalg.eigvalsh(Dn).min() < 0
+
+
+def test_openmp_baseline_matches_serial_oracle():
+    """The multi-core CPU baseline (timed by the bench, not a parity
+    reference) computes the same CG: on the 20^3 uniform cube at rtol 1e-10
+    its solution is within 1e-10 of the serial oracle's and its iteration
+    count within 2 (it only sums its dot products in another order)."""
+    pr = P.cube_uniform(20)
+    ref = oracle.cg(pr.A, pr.b, tol=pr.tol)
+    omp = oracle.cg_omp(pr.A, pr.b, tol=pr.tol)
+    assert omp["status"] == oracle.OK == ref["status"]
+    assert abs(omp["iters"] - ref["iters"]) <= 2
+    assert np.linalg.norm(omp["x"] - ref["x"]) <= 1e-10 * np.linalg.norm(ref["x"])
+    assert oracle.omp_threads() >= 1
+    z = oracle.cg_omp(pr.A, np.zeros(pr.A.n), tol=1e-8)
+    assert z["status"] == oracle.OK and z["iters"] == 0 and not np.any(z["x"])
+    capped = oracle.cg_omp(pr.A, pr.b, tol=1e-14, maxit=5)
+    assert capped["status"] == oracle.ENOCONV and capped["iters"] == 5
