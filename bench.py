@@ -43,14 +43,14 @@ def parse_args():
     ap.add_argument("--impl", choices=["gbcg", "reference"], default="gbcg")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
-    ap.add_argument("--section", choices=["spmv", "forms", "forms100", "batched", "batched_full", "learned",
-                                          "learned_iter"],
+    ap.add_argument("--section", choices=["spmv", "forms", "forms100", "batched", "batched_small", "learned",
+                                          "learned_iter", "fp64peak"],
                     help="run one extra section alone and print its JSON: the 100^3 SpMV roofline, the "
                          "other forms on the 50^3 workload, the forms on the 100^3 system, "
-                         "the 64-system batch, the full 256-system batch, "
-                         "the learned preconditioner (training and tests), or the time per flexible-CG "
-                         "iteration with an untrained network at 50^3 and 100^3")
-    ap.add_argument("--batched-full", action="store_true", help="same as --section batched_full")
+                         "the 256-system batch (edges 20..80), a 64-system batch (edges 20..40), "
+                         "the learned preconditioner (training and tests), the time per flexible-CG "
+                         "iteration with an untrained network at 50^3 and 100^3, or the FP64 peak probe")
+    ap.add_argument("--batched-full", action="store_true", help="same as --section batched")
     ap.add_argument("--learned-only", action="store_true", help="same as --section learned")
     return ap.parse_args()
 
@@ -67,9 +67,20 @@ def flops_per_iteration(n: int, nnz: int, precond: bool) -> int:
     return 2 * nnz + 10 * n + (3 * n if precond else 0)
 
 
-# FP64 peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
-# clock x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+def fp64_peak(stream) -> dict:
+    """FP64 throughput of this GPU, measured in this run (cg_fp64_peak: 4 x SMs
+    CTAs x 512 threads, 8 independent FMA chains per thread, CUDA events),
+    next to the nominal figure from the device's SM count and the maximum SM
+    clock (2 FP64 FMA per clock per SM)."""
+    import torch
+
+    from paper_1107_0538_gb300 import gbcg
+    rc, flops, ms = gbcg.cg_fp64_peak(stream.cuda_stream, 20000)
+    if rc != gbcg.CG_OK or ms <= 0:
+        raise RuntimeError(f"cg_fp64_peak failed: {gbcg.cg_strerror(rc)}")
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return {"tflops": round(flops / ms / 1e9, 4), "ms": round(ms, 3), "sms": sms,
+            "method": "cg_fp64_peak: 4 x SMs CTAs x 512 threads x 8 independent FP64 FMA chains, CUDA events"}
 
 
 def spmv_bytes(n: int, nnz: int) -> int:
@@ -94,6 +105,7 @@ KERNEL_SOURCES = {
     "cg_sellmem_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
     "sell_spmv_kernel": ["gbcg.cu", "sell.cuh", "plan.h"],
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
+    "cg_irsell_kernel": ["gbcg.cu", "sell.cuh", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
     "conv16_kernel": ["learn.cu"] + _COMMON,
     "conv16tc_kernel": ["learn.cu"] + _COMMON,
@@ -236,34 +248,51 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
-def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sample: int) -> dict:
+def generate_batch(nsys: int, emin: int, emax: int, seed0: int = 1000, threads: int = 16) -> list:
+    """problems.batch_systems, one system per task on a thread pool (numpy
+    releases the GIL in the array work): the same systems, generated faster."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1107_0538_gb300 import problems
+    with ThreadPoolExecutor(max(1, min(threads, os.cpu_count() or 1))) as ex:
+        return list(ex.map(lambda i: problems.batch_systems(1, emin, emax, seed0=seed0 + i)[0], range(nsys)))
+
+
+def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune_sys: int, sample: int) -> dict:
     """Batched mixed-precision solves of nsys uneven Q1 boxes x 4 source-current
-    right-hand sides in one persistent launch; optional autotuning; CUDA graph
-    capture of the enqueue; error of sampled pairs against a tight FP64 GPU solve."""
+    right-hand sides in one persistent launch (FP32 inner CG with Jacobi, FP64
+    refinement, rel. residual 1e-8): ms per batch, the same enqueue captured
+    in a CUDA graph and replayed, the autotuner's choice on the first tune_sys
+    systems, and the error of sampled pairs against a tight FP64 GPU solve."""
     import torch
 
-    from paper_1107_0538_gb300 import gbcg, problems
+    from paper_1107_0538_gb300 import gbcg
     t0 = time.perf_counter()
-    sl = problems.batch_systems(nsys, emin, emax, seed0=1000)
+    sl = generate_batch(nsys, emin, emax)
     gen_s = time.perf_counter() - t0
     n_tot = sum(s["A"].n for s in sl)
     nnz_tot = sum(s["A"].nnz for s in sl)
     dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"workload": f"{nsys} Q1 boxes, edges U{{{emin}..{emax}}}, contrast log-U[1e2, 1e4], 4 source-current rhs "
+                       f"each, FP32 inner CG (Jacobi) + FP64 refinement to rel. residual {TOL:g}",
+           "systems": nsys, "rhs": 4, "n_total": n_tot, "nnz_total": nnz_tot, "generate_s": round(gen_s, 2)}
+    if tune_sys:
+        sub = sl[:tune_sys]
+        with gbcg.BatchSolver([x["A"] for x in sub], inner_values=gbcg.CG_VALUES_FP32,
+                              precond=gbcg.CG_PRECOND_JACOBI) as tb:
+            Bt = torch.from_numpy(np.concatenate([x["B"] for x in sub], axis=1)).to(dev).contiguous()
+            rc, ch = tb.tune(Bt, torch.zeros_like(Bt), TOL)
+            out["tuned"] = {"on": f"the first {tune_sys} systems", "status": rc, "inner_tol": ch.inner_tol,
+                            "gather_tiles": ch.gather_tiles, "trials": ch.trials, "best_ms": round(ch.best_ms, 3)}
+            del Bt
+    stream = torch.cuda.Stream()
     t0 = time.perf_counter()
-    bs = gbcg.BatchSolver([s["A"] for s in sl], inner_values=gbcg.CG_VALUES_FP32,
-                          precond=gbcg.CG_PRECOND_JACOBI)
-    create_s = time.perf_counter() - t0
-    Bh = np.concatenate([s["B"] for s in sl], axis=1)
-    B = torch.from_numpy(Bh).to(dev).contiguous()
+    bs = gbcg.BatchSolver([x["A"] for x in sl], inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI,
+                          stream=stream)
+    out["create_s"] = round(time.perf_counter() - t0, 2)
+    B = torch.from_numpy(np.concatenate([x["B"] for x in sl], axis=1)).to(dev).contiguous()
     X = torch.zeros_like(B)
-    out = {"workload": f"{nsys} Q1 boxes, edges U{{{emin}..{emax}}}, contrast 1e2-1e4, 4 source-current rhs, "
-                       f"FP32 inner (Jacobi) + FP64 refinement to rel. residual {TOL:g}",
-           "systems": nsys, "rhs": 4, "n_total": n_tot, "nnz_total": nnz_tot,
-           "generate_s": round(gen_s, 2), "create_s": round(create_s, 2)}
-    if tune:
-        rc, ch = bs.tune(B, X, TOL)
-        out["tuned"] = {"status": rc, "inner_tol": ch.inner_tol, "gather_tiles": ch.gather_tiles,
-                        "trials": ch.trials, "best_ms": round(ch.best_ms, 3)}
+    torch.cuda.synchronize()
     rc, res, ms = bs.solve(B, X, TOL)  # warm-up
     times = []
     for _ in range(steps):
@@ -277,28 +306,27 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sam
                 "ms_per_solve_amortised": round(batch_ms / len(res), 4),
                 "inner_iters_max": max(r.iters for r in res), "outer_max": max(r.outer for r in res),
                 "relres_max": max(r.relres for r in res)})
-    # graph capture of one enqueue
+    # the whole batch's enqueue (copies, memsets, the cooperative launch)
+    # captured in one CUDA graph and replayed
     try:
         g = torch.cuda.CUDAGraph()
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            bsg = gbcg.BatchSolver([x["A"] for x in sl[:min(nsys, 8)]], inner_values=gbcg.CG_VALUES_FP32,
-                                   precond=gbcg.CG_PRECOND_JACOBI, stream=s)
-            n8 = bsg.n
-            Bg = B[:, :n8].contiguous()
-            Xg = torch.zeros_like(Bg)
-            bsg.enqueue(Bg, Xg, TOL)  # warm-up outside the capture
-            torch.cuda.synchronize()
-            with torch.cuda.graph(g, stream=s):
-                bsg.enqueue(Bg, Xg, TOL)
-        Xg.zero_()
-        g.replay()
         torch.cuda.synchronize()
-        rcg, resg = bsg.results(4)
-        out["graph"] = {"captured": True, "replay_status": rcg,
-                        "pairs_converged": sum(1 for r in resg if r.status == gbcg.CG_OK)}
-        bsg.close()
+        with torch.cuda.graph(g, stream=stream):
+            rcq = bs.enqueue(B, X, TOL)
+        X.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+        e1.synchronize()
+        rcg, resg = bs.results(4)
+        out["graph"] = {"captured": rcq == gbcg.CG_OK, "replay_ms": round(e0.elapsed_time(e1), 3),
+                        "replay_status": rcg, "pairs_converged": sum(1 for r in resg if r.status == gbcg.CG_OK),
+                        "systems": nsys}
+        del g
     except Exception as exc:  # report, do not hide
         out["graph"] = {"captured": False, "error": str(exc)[:200]}
     # error of sampled pairs against a tight FP64 CG solve on the GPU
@@ -317,19 +345,23 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune: bool, sam
             errs.append(float(np.linalg.norm(x - ref) / np.linalg.norm(ref)))
         fs.close()
     out["err_vs_fp64_cg_max"] = max(errs) if errs else None
-    out["err_sample"] = (f"{len(errs)} pairs of the {len(order)} smallest systems, against FP64 Jacobi-PCG "
-                         f"on the GPU to rel. residual 1e-13")
+    out["err_sample"] = (f"{len(errs)} pairs of the {len(order)} smallest systems (graph replay's X), against "
+                         f"FP64 Jacobi-PCG on the GPU to rel. residual 1e-13")
     bs.close()
+    del B, X
+    torch.cuda.empty_cache()
     return out
 
 
 def measure_learned(ninst: int = 40, per: int = 500, seg: int = 8, batch: int = 8, lr: float = 1e-3,
-                    reps: int = 3) -> dict:
+                    reps: int = 3, epochs: int = 3, nheld: int = 2) -> dict:
     """The learned preconditioner end to end on the GPU: training pairs from
     restarted FP64 CG on ninst random 50^3 instances (contrast 1e3, seeds
-    10000+), one epoch of Adam through the project's kernels, then flexible CG
-    with the network against FP64 CG and Jacobi-PCG on the 50^3 workload and
-    on an unseen 100^3 instance (seed 20000), to rel. residual 1e-8."""
+    10000+), `epochs` epochs of Adam through the project's kernels with the
+    loss on held-out pairs (nheld instances never trained on, seeds 15000+)
+    after each, then flexible CG with the network against FP64 CG and
+    Jacobi-PCG on the 50^3 workload and on an unseen 100^3 instance (seed
+    20000), to rel. residual 1e-8."""
     import torch
 
     from paper_1107_0538_gb300 import gbcg, problems
@@ -358,19 +390,39 @@ def measure_learned(ninst: int = 40, per: int = 500, seg: int = 8, batch: int = 
     out["pairs_s"] = round(time.perf_counter() - t0, 2)
     pinst = np.repeat(np.arange(ninst), per)
     lset = gbcg.LearnSet(solvers, pinst, R, E)
-    held = np.arange(0, len(pinst), max(1, len(pinst) // 256))
-    loss0, _ = net.grad(lset, held)
+    # held-out pairs: the same recipe on instances the network never trains on
+    held_inst = [problems.learn_instance(50, 15000 + i) for i in range(nheld)]
+    held_solvers = []
+    Rh = torch.empty((nheld * per, n), dtype=torch.float32, device=dev)
+    Eh = torch.empty_like(Rh)
+    for k, inst in enumerate(held_inst):
+        s = gbcg.Solver(inst.A, precond=gbcg.CG_PRECOND_LEARNED)
+        s.set_learned(net, inst.grid, inst.lognu.astype(np.float32))
+        s.learn_pairs(torch.from_numpy(inst.b).to(dev), torch.from_numpy(inst.xstar).to(dev), seg, per,
+                      Rh[k * per:(k + 1) * per], Eh[k * per:(k + 1) * per])
+        held_solvers.append(s)
+    hset = gbcg.LearnSet(held_solvers, np.repeat(np.arange(nheld), per), Rh, Eh)
+    held = np.arange(nheld * per)
+    sample = np.arange(0, len(pinst), max(1, len(pinst) // 256))
     steps = len(pinst) // batch
-    order = (problems.splitmix64(77, steps * batch) % np.uint64(len(pinst))).astype(np.int64)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    net.train(lset, order, steps, batch, lr)
-    torch.cuda.synchronize()
-    out["train"] = {"steps": steps, "batch": batch, "lr": lr, "epochs": 1, "s": round(time.perf_counter() - t0, 2),
-                    "held_out_loss_before": round(loss0, 5), "held_out_loss_after": round(net.grad(lset, held)[0], 5),
-                    "held": f"{len(held)} training pairs, every {max(1, len(pinst) // 256)}th"}
-    del R, E, lset
-    for s in solvers:
+    curve = [{"epoch": 0, "held_out_loss": round(net.grad(hset, held)[0], 5),
+              "train_sample_loss": round(net.grad(lset, sample)[0], 5)}]
+    train_s = 0.0
+    for ep in range(epochs):
+        order = (problems.splitmix64(77 + ep, steps * batch) % np.uint64(len(pinst))).astype(np.int64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.train(lset, order, steps, batch, lr)
+        torch.cuda.synchronize()
+        train_s += time.perf_counter() - t0
+        curve.append({"epoch": ep + 1, "held_out_loss": round(net.grad(hset, held)[0], 5),
+                      "train_sample_loss": round(net.grad(lset, sample)[0], 5)})
+    out["train"] = {"steps_per_epoch": steps, "batch": batch, "lr": lr, "epochs": epochs, "s": round(train_s, 2),
+                    "loss_by_epoch": curve,
+                    "held_out": f"{nheld * per} pairs from {nheld} 50^3 instances not trained on (seeds 15000+)",
+                    "train_sample": f"{len(sample)} training pairs, every {max(1, len(pinst) // 256)}th"}
+    del R, E, lset, Rh, Eh, hset
+    for s in solvers + held_solvers:
         s.close()
     torch.cuda.empty_cache()
 
@@ -476,7 +528,7 @@ def measure_forms(pr, ms_fp64: float, iters_fp64: int, count: int, x_ref, flush)
     return forms
 
 
-def measure_forms_100cube(flush, count: int = 2) -> dict:
+def measure_forms_100cube(flush, fp64_tflops: float, count: int = 2) -> dict:
     """The mixed-precision forms on the 100^3 system (N=1030301, NNZ=27270901,
     contrast 1e3, b = A x*): the FP64 matrix (327 MB of CSR) no longer fits
     the L2, so the 8- and 6-byte inner entries of FP32/BF16 refinement cut
@@ -513,11 +565,15 @@ def measure_forms_100cube(flush, count: int = 2) -> dict:
             kern_s = statistics.mean(i.kernel_ms for _, i in res_v) / 1e3
             flops = info_v.iters * flops_per_iteration(big.A.n, big.A.nnz, False)
             tr = ncu_traffic(kern)
-            out["roofline"] = {"bound": "alu", "kernel": kern, "achieved": round(flops / kern_s / 1e12, 4),
-                               "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-                               "frac": round(flops / kern_s / 1e12 / FP64_PEAK_TFLOPS, 4),
+            nbytes = info_v.iters * bytes_per_iteration(big.A.n, big.A.nnz, False)
+            hbm = measured_peaks()["hbm_gbs"]
+            out["roofline"] = {"bound": "hbm", "kernel": kern, "achieved": round(nbytes / kern_s / 1e9, 1),
+                               "peak": hbm, "unit": "GB/s", "frac": round(nbytes / kern_s / 1e9 / hbm, 4),
                                "traffic": (round(tr["dram_bytes_per_launch"]) if tr else None),
-                               "algorithmic_flops_per_launch": flops}
+                               "algorithmic_bytes_per_launch": nbytes,
+                               "fp64_achieved_tflops": round(flops / kern_s / 1e12, 4),
+                               "fp64_peak_tflops": fp64_tflops,
+                               "fp64_frac": round(flops / kern_s / 1e12 / fp64_tflops, 4)}
         out[name] = {"ms_per_solve": round(v_ms, 3), "iters": info_v.iters, "outer": info_v.outer,
                      "relres_true": info_v.relres_true,
                      "err_vs_fp64_cg": float(np.linalg.norm(xv - x_fp64) / np.linalg.norm(x_fp64)),
@@ -527,7 +583,7 @@ def measure_forms_100cube(flush, count: int = 2) -> dict:
     return out
 
 
-def measure_spmv_hbm(peaks: dict, flush) -> dict:
+def measure_spmv_hbm(peaks: dict, flush, fp64_tflops: float) -> dict:
     """One FP64 SpMV (cg_spmv: the SELL-32 kernel) on the 100^3 system (27.3M
     entries), L2 flushed before each of 20 launches, median time against the
     measured HBM peak."""
@@ -562,7 +618,7 @@ def measure_spmv_hbm(peaks: dict, flush) -> dict:
         "kernel": "sell_spmv_kernel", "us": round(t_med * 1e6, 2), "achieved": round(gbs, 1),
         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
         "algorithmic_bytes": sb,
-        "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / FP64_PEAK_TFLOPS, 4),
+        "fp64_frac": round(2 * big.A.nnz / t_med / 1e12 / fp64_tflops, 4),
         "traffic": (round(trs["dram_bytes_per_launch"]) if trs else None),
     }
 
@@ -603,9 +659,9 @@ def run_section(args) -> None:
     from paper_1107_0538_gb300 import gbcg, problems
     torch.cuda.set_device(0)
     gbcg.lib()
-    name = "batched_full" if args.batched_full else "learned" if args.learned_only else args.section
+    name = "batched" if args.batched_full else "learned" if args.learned_only else args.section
     if name == "spmv":
-        out = measure_spmv_hbm(measured_peaks(), l2_flush_buffer())
+        out = measure_spmv_hbm(measured_peaks(), l2_flush_buffer(), fp64_peak(torch.cuda.current_stream())["tflops"])
     elif name == "forms":
         flush = l2_flush_buffer()
         pr = problems.cube_blobs(50)
@@ -617,11 +673,13 @@ def run_section(args) -> None:
         s.close()
         out = measure_forms(pr, statistics.mean(t for t, _ in res), res[-1][1].iters, 3, None, flush)
     elif name == "forms100":
-        out = measure_forms_100cube(l2_flush_buffer())
+        out = measure_forms_100cube(l2_flush_buffer(), fp64_peak(torch.cuda.current_stream())["tflops"])
     elif name == "batched":
-        out = measure_batched(64, 20, 40, 3, tune=True, sample=2)
-    elif name == "batched_full":
-        out = measure_batched(256, 20, 80, max(1, args.steps // 5), tune=False, sample=2)
+        out = measure_batched(256, 20, 80, 1, tune_sys=32, sample=2)
+    elif name == "batched_small":
+        out = measure_batched(64, 20, 40, 3, tune_sys=64, sample=2)
+    elif name == "fp64peak":
+        out = fp64_peak(torch.cuda.current_stream())
     elif name == "learned_iter":
         out = measure_learned_iter()
     else:
@@ -682,17 +740,24 @@ def run_gbcg(args) -> None:
     # (systems up to 31 slices per CTA) or the tiled kernel
     solve_kernel = "cg_sell_kernel" if solver.plan()["slice_solve"] else "cg_solve_kernel"
     tr = ncu_traffic(solve_kernel)
+    fp64 = fp64_peak(stream)
+    nominal = fp64["sms"] * 2 * 2 * (clk.summary()["sm_max_mhz"] or 2070.0) * 1e6 / 1e12
+    # the bytes view of the CG iteration's algorithmic bytes (12 NNZ + 4(N+1) +
+    # 88 N per iteration) against the measured HBM copy peak; at this size an
+    # iteration's bytes stay in L2, so this is the L2-effective rate, and the
+    # DRAM traffic (ncu) is the matrix read once per solve
     roofline = {
-        "bound": "alu", "kernel": solve_kernel, "achieved": round(achieved_tflops, 4),
-        "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-        "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
-        "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+        "bound": "hbm", "kernel": solve_kernel, "achieved": round(achieved_gbs, 1),
+        "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
+        "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})",
         "traffic": (round(tr["dram_bytes_per_launch"]) if tr else None),
+        "algorithmic_bytes_per_launch": iters * bpi, "bytes_per_iteration": bpi,
+        "view": "L2-effective: the 53.5 MB an iteration moves stay in the L2",
+        "fp64_achieved_tflops": round(achieved_tflops, 4), "fp64_peak_tflops": fp64["tflops"],
+        "fp64_frac": round(achieved_tflops / fp64["tflops"], 4),
+        "fp64_peak_source": "measured in this run: " + fp64["method"],
+        "fp64_peak_nominal_tflops": round(nominal, 4),
         "algorithmic_flops_per_launch": iters * fpi,
-        "hbm_view": {"achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(achieved_gbs / peaks["hbm_gbs"], 4),
-                     "algorithmic_bytes_per_launch": iters * bpi,
-                     "note": "53.5 MB per iteration stays in the 126 MB L2; HBM is read once per solve"},
     }
 
     line = {
@@ -731,22 +796,34 @@ def run_gbcg(args) -> None:
     solver.close()
 
     if not args.no_extras:
-        # ------------------- CPU oracle baseline (its solution is the reference
-        # the other forms' errors are reported against)
+        # ------------------- CPU baselines: the OpenMP build on all host cores
+        # and the serial oracle (whose solution the other forms' errors are
+        # reported against)
         x_oracle = None
         if rank == 0 and world == 1:
             import oracle
+            r = oracle.cg_omp(pr.A, pr.b, tol=TOL)   # warm-up (thread pool, pages)
+            t0 = time.perf_counter()
+            r = oracle.cg_omp(pr.A, pr.b, tol=TOL)
+            dt = (time.perf_counter() - t0) * 1e3
+            assert r["status"] == oracle.OK
+            line["cpu_baseline"] = {
+                "value": round(dt, 2), "unit": UNIT, "cores": oracle.omp_threads(), "kind": "oracle",
+                "build": "OpenMP (row and vector loops over all host cores), beside the serial oracle",
+                "sample": f"one full FP64 CG solve of the same system ({r['iters']} iterations)"}
             t0 = time.perf_counter()
             r = oracle.cg(pr.A, pr.b, tol=TOL)
             dt = (time.perf_counter() - t0) * 1e3
             x_oracle = r["x"]
-            line["cpu_baseline"] = {
+            line["cpu_baseline_serial"] = {
                 "value": round(dt, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"one full serial FP64 CG solve of the same system ({r['iters']} iterations)"}
         forms = measure_forms(pr, ms_per_step, iters, max(3, args.steps // 2), x_oracle, flush)
-        line["spmv_hbm"] = measure_spmv_hbm(peaks, flush)
-        line["forms_100cube"] = measure_forms_100cube(flush)
-        line["batched"] = measure_batched(64, 20, 40, 3, tune=True, sample=2)
+        line["spmv_hbm"] = measure_spmv_hbm(peaks, flush, fp64["tflops"])
+        line["roofline"]["spmv_hbm_frac"] = line["spmv_hbm"]["frac"]
+        line["roofline"]["spmv_hbm_gbs"] = line["spmv_hbm"]["achieved"]
+        line["forms_100cube"] = measure_forms_100cube(flush, fp64["tflops"])
+        line["batched"] = measure_batched(256, 20, 80, 1, tune_sys=32, sample=2)
         line["learned"] = measure_learned()
         lf = line["learned"]["q1_50cube_c2"]["learned_fcg"]
         forms["learned_fcg"] = {"ms_per_solve": lf["ms_per_solve"], "iters": lf["iters"],

@@ -129,3 +129,32 @@ def test_batch_tuner_and_async(dev):
         rc, res = bs.results(4)
         assert rc == gbcg.CG_OK
         check_pairs(sl, X.cpu().numpy(), res, 4, 1)
+
+
+def test_batch_graph_capture_replay_matches_oracle(dev):
+    """cg_batch_enqueue makes no host synchronization and allocates nothing,
+    so one enqueue is captured into a CUDA graph on the handle's stream; two
+    replays from x0 = 0 must each give pairs that pass the oracle checks."""
+    sl = systems(6)
+    stream = torch.cuda.Stream()
+    with gbcg.BatchSolver([s["A"] for s in sl], precond=1, stream=stream) as bs:
+        B = torch.from_numpy(stacked(sl, 4)).to(dev).contiguous()
+        X = torch.zeros_like(B)
+        torch.cuda.synchronize()
+        assert bs.enqueue(B, X, TOL) == gbcg.CG_OK   # once outside the capture
+        rc, res = bs.results(4)
+        assert rc == gbcg.CG_OK
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            rcq = bs.enqueue(B, X, TOL)
+        assert rcq == gbcg.CG_OK
+        for _ in range(2):
+            X.zero_()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                g.replay()
+            rc, res = bs.results(4)
+            assert rc == gbcg.CG_OK
+            check_pairs(sl, X.cpu().numpy(), res, 4, 1)
+        del g
