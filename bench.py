@@ -276,6 +276,7 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune_sys: int, 
     out = {"workload": f"{nsys} Q1 boxes, edges U{{{emin}..{emax}}}, contrast log-U[1e2, 1e4], 4 source-current rhs "
                        f"each, FP32 inner CG (Jacobi) + FP64 refinement to rel. residual {TOL:g}",
            "systems": nsys, "rhs": 4, "n_total": n_tot, "nnz_total": nnz_tot, "generate_s": round(gen_s, 2)}
+    choice = None
     if tune_sys:
         sub = sl[:tune_sys]
         with gbcg.BatchSolver([x["A"] for x in sub], inner_values=gbcg.CG_VALUES_FP32,
@@ -283,13 +284,19 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune_sys: int, 
             Bt = torch.from_numpy(np.concatenate([x["B"] for x in sub], axis=1)).to(dev).contiguous()
             rc, ch = tb.tune(Bt, torch.zeros_like(Bt), TOL)
             out["tuned"] = {"on": f"the first {tune_sys} systems", "status": rc, "inner_tol": ch.inner_tol,
-                            "gather_tiles": ch.gather_tiles, "trials": ch.trials, "best_ms": round(ch.best_ms, 3)}
+                            "gather_tiles": ch.gather_tiles, "lanes_per_row": ch.lanes_per_row,
+                            "trials": ch.trials, "best_ms": round(ch.best_ms, 3),
+                            "space": "inner tol {1e-2, 3e-3, 1e-3, 1e-4} x tiles {x-window, gather} x "
+                                     "rows per warp step {32, 16, 8}"}
+            choice = (ch.inner_tol, ch.gather_tiles, ch.lanes_per_row) if rc == gbcg.CG_OK else None
             del Bt
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     bs = gbcg.BatchSolver([x["A"] for x in sl], inner_values=gbcg.CG_VALUES_FP32, precond=gbcg.CG_PRECOND_JACOBI,
                           stream=stream)
     out["create_s"] = round(time.perf_counter() - t0, 2)
+    if tune_sys and choice is not None:
+        bs.set_tuning(*choice)   # the sub-batch's choice applied to the whole batch
     B = torch.from_numpy(np.concatenate([x["B"] for x in sl], axis=1)).to(dev).contiguous()
     X = torch.zeros_like(B)
     torch.cuda.synchronize()

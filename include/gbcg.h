@@ -259,13 +259,17 @@ typedef struct {
     double relres;           /* ||b - A x||_2 / ||b||_2 (FP64) at the last check  */
 } cg_batch_result;
 
-/* What cg_batch_tune chose. */
+/* What cg_batch_tune chose (also the argument of cg_batch_set_tuning). */
 typedef struct {
     double inner_tol;        /* inner tolerance of the fastest trial             */
     int32_t gather_tiles;    /* 1: tiles gather x from memory instead of staging
                                 x-windows                                       */
     int32_t trials;
     double best_ms;          /* device time of the fastest trial                 */
+    int32_t lanes_per_row;   /* lanes that share one row in the inner SpMM: 1, 2
+                                or 4 (a warp steps through a 32-row tile 32, 16
+                                or 8 rows at a time)                              */
+    int32_t reserved;        /* 0                                                 */
 } cg_batch_tuning;
 
 typedef struct cg_batch cg_batch;
@@ -312,13 +316,23 @@ int cg_batch_solve(cg_batch *h, const double *B, double *X, int32_t nrhs, double
                    cg_batch_result *results, double *kernel_ms);
 
 /*
- * Autotuner: times full solves of B (x0 from X, X left unchanged) for each
- * inner tolerance in {1e-2, 3e-3, 1e-3, 1e-4} (BF16: >= 1e-3) with staged
- * x-windows and with gather tiles, keeps the fastest converged choice for
- * later solves and reports it in *choice (may be NULL).
+ * Autotuner: times full solves of B (x0 from X, X left unchanged) for every
+ * combination of the inner tolerance in {1e-2, 3e-3, 1e-3, 1e-4} (BF16:
+ * >= 1e-3), the tile kind (staged x-windows or gather tiles) and the rows a
+ * warp takes per step of the inner SpMM (32, 16 or 8: 1, 2 or 4 lanes per
+ * row), keeps the fastest converged choice for later solves and reports it
+ * in *choice (may be NULL).  Synchronous.
  */
 int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol,
                   cg_batch_tuning *choice);
+
+/*
+ * Applies a choice (for example one cg_batch_tune found on a smaller batch
+ * of the same kind of systems): inner_tol in (0, 1), gather_tiles 0 or 1,
+ * lanes_per_row 1, 2 or 4; trials and best_ms are ignored.  CG_EINVAL
+ * otherwise.  Takes effect at the next enqueue.
+ */
+int cg_batch_set_tuning(cg_batch *h, const cg_batch_tuning *choice);
 
 /* Frees the batch handle (NULL is a no-op). */
 void cg_batch_destroy(cg_batch *h);

@@ -66,6 +66,7 @@ struct BatchParams {
     const int32_t *cta_seg0;     // first segment of each CTA (ctas + 1)
     const int32_t *sys_seg0;     // first segment of each system (nsys + 1)
     int32_t nsys, nrhs, nseg;
+    int32_t lanes_per_row;       // SpMM rows per warp step: 32 / lanes_per_row (1, 2 or 4 lanes per row)
     double tol, inner_tol;
     int32_t maxit, max_outer, max_inner;
     const double *B;             // caller's right-hand sides, column r at B + r * n
@@ -97,6 +98,11 @@ __device__ __forceinline__ float4 fma_acc(float v, float4 x, float4 a) {
 }
 __device__ __forceinline__ float4 fma_acc(__nv_bfloat16 v, float4 x, float4 a) {
     return fma_acc(__bfloat162float(v), x, a);
+}
+__device__ __forceinline__ double xor_add(double v, int m) { return v + __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ float4 xor_add(float4 v, int m) {
+    return make_float4(v.x + __shfl_xor_sync(0xffffffffu, v.x, m), v.y + __shfl_xor_sync(0xffffffffu, v.y, m),
+                       v.z + __shfl_xor_sync(0xffffffffu, v.z, m), v.w + __shfl_xor_sync(0xffffffffu, v.w, m));
 }
 __device__ __forceinline__ double warp_sum_acc(double v) { return warp_sum(v); }
 __device__ __forceinline__ float4 warp_sum_acc(float4 v) {
@@ -235,20 +241,32 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
                 for (int k = d.a + lane; k < d.e; k += 32) part = fma_acc(vals[k], x[P.colidx[k]], part);
                 part = warp_sum_acc(part);
                 if (lane == 0) rowfn(sys, d.r0, part, acc);
-            } else if (row < d.r1) {
+            } else {
+                // the tile's rows in steps of 32 / L rows, L = lanes_per_row
+                // lanes per row (lane l takes entries k0 + l mod L, + L, ...;
+                // the L partial sums are joined by a butterfly)
                 const VT *vs = S.vals<VT, XT>(w) - (d.a & ~(16 / (int)sizeof(VT) - 1));
                 const int32_t *rs = S.rptr<VT, XT>(w) - (d.r0 & ~3);
-                const int k0 = rs[row], k1 = rs[row + 1];
-                AT sum{};
-                if (d.kind == kTileWindow) {
-                    const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols<VT, XT>(w)) - (d.a & ~7);
-                    const XT *win = S.win<VT, XT>(w);
-                    for (int k = k0; k < k1; ++k) sum = fma_acc(vs[k], win[lc[k]], sum);
-                } else {
-                    const int32_t *cs = S.cols<VT, XT>(w) - (d.a & ~3);
-                    for (int k = k0; k < k1; ++k) sum = fma_acc(vs[k], x[cs[k]], sum);
+                const int L = B.lanes_per_row, lg = L == 4 ? 2 : (L == 2 ? 1 : 0);
+                const int sub = lane & (L - 1);
+                for (int step = 0; step < 32; step += 32 / L) {
+                    const int rw = d.r0 + step + (lane >> lg);
+                    AT sum{};
+                    if (rw < d.r1) {
+                        const int k0 = rs[rw], k1 = rs[rw + 1];
+                        if (d.kind == kTileWindow) {
+                            const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols<VT, XT>(w)) - (d.a & ~7);
+                            const XT *win = S.win<VT, XT>(w);
+                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], win[lc[k]], sum);
+                        } else {
+                            const int32_t *cs = S.cols<VT, XT>(w) - (d.a & ~3);
+                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], x[cs[k]], sum);
+                        }
+                    }
+                    for (int m = 1; m < L; m <<= 1) sum = xor_add(sum, m);
+                    if (rw < d.r1 && sub == 0) rowfn(sys, rw, sum, acc);
+                    if (d.r0 + step + 32 / L >= d.r1) break;   // warp-uniform
                 }
-                rowfn(sys, row, sum, acc);
             }
             __syncwarp();
             ++count;
@@ -545,6 +563,7 @@ struct cg_batch {
     int64_t nnz = 0;
     double inner_tol = 1e-3;
     int use_gather = 0;                 // tuned: 1 = gather tiles instead of x-windows
+    int lanes_per_row = 1;              // tuned: SpMM lanes per row (rows per warp step 32 / this)
     std::vector<int32_t> sys_rows;
     // device
     int32_t *rowptr = nullptr, *colidx = nullptr, *tile_sys = nullptr, *cta_tile = nullptr;
@@ -631,6 +650,7 @@ BatchParams batch_params(const cg_batch *h, const double *Bm, int nrhs, double t
     B.nsys = h->nsys;
     B.nrhs = nrhs;
     B.nseg = h->nseg;
+    B.lanes_per_row = h->lanes_per_row;
     B.tol = tol;
     B.inner_tol = h->inner_tol;
     B.maxit = maxit;
@@ -919,39 +939,59 @@ int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double 
     cudaGetDevice(&prev);
     if (prev != h->device) cudaSetDevice(h->device);
     const double tols[] = {1e-2, 3e-3, 1e-3, 1e-4};
+    const int lanes[] = {1, 2, 4};
     double best_ms = 1e300, best_tol = h->inner_tol;
-    int best_gather = h->use_gather, tried = 0, rc = CG_OK;
+    int best_gather = h->use_gather, best_lanes = h->lanes_per_row, tried = 0, rc = CG_OK;
     for (int gather = 0; gather < 2 && rc == CG_OK; ++gather) {
-        for (double it : tols) {
-            if (h->opts.inner_values == CG_VALUES_BF16 && it < 1e-3) continue;  // beyond BF16's refinement
-            h->inner_tol = it;
-            h->use_gather = gather;
-            float ms = 0.0f;
-            // x0 from X, result not copied back: the caller's X is left as it was
-            if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) { rc = CG_ECUDA; break; }
-            int r = batch_enqueue(h, B, X, nrhs, tol, std::max(h->n, 1), false);
-            if (r == CG_OK && cudaEventRecord(h->ev1, h->stream) != cudaSuccess) r = CG_ECUDA;
-            if (r == CG_OK) r = batch_collect(h, nullptr);
-            if (r == CG_ECUDA || r == CG_ETIMEOUT) { rc = r; break; }
-            cudaEventElapsedTime(&ms, h->ev0, h->ev1);
-            ++tried;
-            if (r == CG_OK && ms < best_ms) {
-                best_ms = ms;
-                best_tol = it;
-                best_gather = gather;
+        for (int L : lanes) {
+            for (double it : tols) {
+                if (h->opts.inner_values == CG_VALUES_BF16 && it < 1e-3) continue;  // beyond BF16's refinement
+                h->inner_tol = it;
+                h->use_gather = gather;
+                h->lanes_per_row = L;
+                float ms = 0.0f;
+                // x0 from X, result not copied back: the caller's X is left as it was
+                if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) { rc = CG_ECUDA; break; }
+                int r = batch_enqueue(h, B, X, nrhs, tol, std::max(h->n, 1), false);
+                if (r == CG_OK && cudaEventRecord(h->ev1, h->stream) != cudaSuccess) r = CG_ECUDA;
+                if (r == CG_OK) r = batch_collect(h, nullptr);
+                if (r == CG_ECUDA || r == CG_ETIMEOUT) { rc = r; break; }
+                cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+                ++tried;
+                if (r == CG_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best_tol = it;
+                    best_gather = gather;
+                    best_lanes = L;
+                }
             }
+            if (rc != CG_OK) break;
         }
     }
     h->inner_tol = best_tol;
     h->use_gather = best_gather;
+    h->lanes_per_row = best_lanes;
     if (choice) {
         choice->inner_tol = best_tol;
         choice->gather_tiles = best_gather;
         choice->trials = tried;
         choice->best_ms = best_ms < 1e300 ? best_ms : -1.0;
+        choice->lanes_per_row = best_lanes;
+        choice->reserved = 0;
     }
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     return rc;
+}
+
+int cg_batch_set_tuning(cg_batch *h, const cg_batch_tuning *choice) {
+    if (!h || !choice) return CG_EINVAL;
+    if (!(choice->inner_tol > 0.0 && choice->inner_tol < 1.0) || (choice->gather_tiles != 0 && choice->gather_tiles != 1) ||
+        (choice->lanes_per_row != 1 && choice->lanes_per_row != 2 && choice->lanes_per_row != 4))
+        return CG_EINVAL;
+    h->inner_tol = choice->inner_tol;
+    h->use_gather = choice->gather_tiles;
+    h->lanes_per_row = choice->lanes_per_row;
+    return CG_OK;
 }
 
 void cg_batch_destroy(cg_batch *h) { batch_free(h); }

@@ -31,7 +31,7 @@ EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_h
            "cg_spmv", "cg_spmv_inner", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_fp64_peak",
            "cg_solve_noalloc",
            "cg_batch_create", "cg_batch_enqueue", "cg_batch_results", "cg_batch_solve",
-           "cg_batch_tune", "cg_batch_destroy", "cg_net_create", "cg_net_get_params",
+           "cg_batch_tune", "cg_batch_set_tuning", "cg_batch_destroy", "cg_net_create", "cg_net_get_params",
            "cg_net_set_params", "cg_net_destroy", "cg_set_learned", "cg_precond_apply", "cg_learn_pairs",
            "cg_learn_grad", "cg_learn_train")
 CG_NOALLOC_MAX_N = 262144
@@ -87,7 +87,8 @@ class cg_batch_result(ctypes.Structure):
 
 class cg_batch_tuning(ctypes.Structure):
     _fields_ = [("inner_tol", ctypes.c_double), ("gather_tiles", ctypes.c_int32),
-                ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double)]
+                ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cg_learn_set(ctypes.Structure):
@@ -147,6 +148,8 @@ def lib() -> ctypes.CDLL:
             L.cg_batch_solve.restype = ctypes.c_int
             L.cg_batch_tune.argtypes = [vp, vp, vp, i32, dbl, ctypes.POINTER(cg_batch_tuning)]
             L.cg_batch_tune.restype = ctypes.c_int
+            L.cg_batch_set_tuning.argtypes = [vp, ctypes.POINTER(cg_batch_tuning)]
+            L.cg_batch_set_tuning.restype = ctypes.c_int
             L.cg_batch_destroy.argtypes = [vp]
             L.cg_batch_destroy.restype = None
             fp = ctypes.POINTER(ctypes.c_float)
@@ -377,6 +380,10 @@ def cg_batch_tune(h: int, b_ptr: int, x_ptr: int, nrhs: int, tol: float) -> tupl
     return rc, t
 
 
+def cg_batch_set_tuning(h: int, choice: cg_batch_tuning) -> int:
+    return lib().cg_batch_set_tuning(ctypes.c_void_p(h), ctypes.byref(choice))
+
+
 def cg_batch_destroy(h: int | None) -> None:
     lib().cg_batch_destroy(ctypes.c_void_p(h or 0))
 
@@ -426,6 +433,12 @@ class BatchSolver:
 
     def tune(self, B, X, tol: float):
         return cg_batch_tune(self.h, B.data_ptr(), X.data_ptr(), B.shape[0], tol)
+
+    def set_tuning(self, inner_tol: float, gather_tiles: int, lanes_per_row: int) -> None:
+        c = cg_batch_tuning(inner_tol=inner_tol, gather_tiles=gather_tiles, lanes_per_row=lanes_per_row)
+        rc = cg_batch_set_tuning(self.h, c)
+        if rc != CG_OK:
+            raise GbcgError(rc, "cg_batch_set_tuning")
 
     def close(self) -> None:
         if getattr(self, "h", None):

@@ -123,7 +123,8 @@ def test_batch_tuner_and_async(dev):
         B = torch.from_numpy(stacked(sl, 4)).to(dev).contiguous()
         X = torch.zeros_like(B)
         rc, choice = bs.tune(B, X, TOL)
-        assert rc == gbcg.CG_OK and choice.trials >= 4 and choice.best_ms > 0
+        assert rc == gbcg.CG_OK and choice.trials == 24 and choice.best_ms > 0
+        assert choice.lanes_per_row in (1, 2, 4) and choice.gather_tiles in (0, 1)
         assert torch.count_nonzero(X) == 0  # the tuner leaves X alone
         assert bs.enqueue(B, X, TOL) == gbcg.CG_OK
         rc, res = bs.results(4)
@@ -158,3 +159,23 @@ def test_batch_graph_capture_replay_matches_oracle(dev):
             assert rc == gbcg.CG_OK
             check_pairs(sl, X.cpu().numpy(), res, 4, 1)
         del g
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+@pytest.mark.parametrize("gather", [0, 1], ids=["window", "gather"])
+def test_batch_tuning_choices_match_oracle(dev, lanes, gather):
+    """Every point the tuner can choose (tile kind x lanes per row of the
+    inner SpMM), applied with cg_batch_set_tuning, gives pairs that pass the
+    oracle checks; invalid choices are refused."""
+    sl = systems(5)
+    with gbcg.BatchSolver([s["A"] for s in sl], precond=1) as bs:
+        bs.set_tuning(3e-3, gather, lanes)
+        B = torch.from_numpy(stacked(sl, 4)).to(dev).contiguous()
+        X = torch.zeros_like(B)
+        rc, res, ms = bs.solve(B, X, TOL)
+        assert rc == gbcg.CG_OK
+        check_pairs(sl, X.cpu().numpy(), res, 4, 1)
+        for bad in (gbcg.cg_batch_tuning(inner_tol=3e-3, gather_tiles=0, lanes_per_row=3),
+                    gbcg.cg_batch_tuning(inner_tol=0.0, gather_tiles=0, lanes_per_row=1),
+                    gbcg.cg_batch_tuning(inner_tol=1e-3, gather_tiles=2, lanes_per_row=1)):
+            assert gbcg.cg_batch_set_tuning(bs.h, bad) == gbcg.CG_EINVAL
