@@ -236,6 +236,16 @@ void cg_destroy(cg_handle *h);
 const char *cg_strerror(int code);
 
 /*
+ * Index faults seen by a library built with -DGBCG_BOUNDS_CHECK (the
+ * bounds-check build, libgbcg_check.so): its kernels test every column index
+ * they gather through and every staged row range they walk, skip a bad one
+ * (an empty range, or index 0) and count it here, for the whole process and
+ * every device.  *count receives the count, or -1 for a normal build (which
+ * checks nothing).  Synchronous.  CG_EINVAL for a NULL count.
+ */
+int cg_bounds_faults(int64_t *count);
+
+/*
  * Measurement helper, not part of the method: the FP64 FMA throughput of the
  * current device, the denominator of the FP64 roofline the solve kernels are
  * reported against (one CG iteration is 2 NNZ + 10 N flops, Table I).  One

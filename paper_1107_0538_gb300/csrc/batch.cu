@@ -34,6 +34,7 @@
 
 #include "cg_device.cuh"
 #include "gbcg.h"
+#include "handle.h"
 #include "lowprec.h"
 #include "plan.h"
 
@@ -238,7 +239,7 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
             const int row = d.r0 + lane;
             if (d.kind == kTileLong) {
                 AT part{};
-                for (int k = d.a + lane; k < d.e; k += 32) part = fma_acc(vals[k], x[P.colidx[k]], part);
+                for (int k = d.a + lane; k < d.e; k += 32) part = fma_acc(vals[k], x[bchk(P.colidx[k], P.n)], part);
                 part = warp_sum_acc(part);
                 if (lane == 0) rowfn(sys, d.r0, part, acc);
             } else {
@@ -253,14 +254,15 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
                     const int rw = d.r0 + step + (lane >> lg);
                     AT sum{};
                     if (rw < d.r1) {
-                        const int k0 = rs[rw], k1 = rs[rw + 1];
+                        int k0 = rs[rw], k1 = rs[rw + 1];
+                        bchk_range(k0, k1, d.a, d.e);
                         if (d.kind == kTileWindow) {
                             const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols<VT, XT>(w)) - (d.a & ~7);
                             const XT *win = S.win<VT, XT>(w);
-                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], win[lc[k]], sum);
+                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], win[bchk(lc[k], kWinMax)], sum);
                         } else {
                             const int32_t *cs = S.cols<VT, XT>(w) - (d.a & ~3);
-                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], x[cs[k]], sum);
+                            for (int k = k0 + sub; k < k1; k += L) sum = fma_acc(vs[k], x[bchk(cs[k], P.n)], sum);
                         }
                     }
                     for (int m = 1; m < L; m <<= 1) sum = xor_add(sum, m);
@@ -714,9 +716,12 @@ int batch_collect(cg_batch *h, cg_batch_result *results) {
 
 }  // namespace
 
+long long gbcg::bounds_faults_batch() { return read_bounds_faults(); }
+
 extern "C" {
 
 int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in, void *stream, cg_batch **out) {
+    NvtxRange nvtx("gbcg.batch_create");
     if (!out) return CG_EINVAL;
     *out = nullptr;
     if (!systems || nsys < 1) return CG_EINVAL;
@@ -899,6 +904,7 @@ int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in,
 }
 
 int cg_batch_enqueue(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol, int32_t maxit) {
+    NvtxRange nvtx("gbcg.batch_enqueue");
     if (!h || !B || !X || nrhs < 1 || nrhs > kRhs || !(tol >= 0.0) || !std::isfinite(tol)) return CG_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -915,6 +921,7 @@ int cg_batch_results(cg_batch *h, cg_batch_result *results) {
 
 int cg_batch_solve(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol, int32_t maxit,
                    cg_batch_result *results, double *kernel_ms) {
+    NvtxRange nvtx("gbcg.batch_solve");
     if (!h || !B || !X || nrhs < 1 || nrhs > kRhs || !(tol >= 0.0) || !std::isfinite(tol)) return CG_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);
@@ -934,6 +941,7 @@ int cg_batch_solve(cg_batch *h, const double *B, double *X, int32_t nrhs, double
 }
 
 int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double tol, cg_batch_tuning *choice) {
+    NvtxRange nvtx("gbcg.batch_tune");
     if (!h || !B || !X || nrhs < 1 || nrhs > kRhs) return CG_EINVAL;
     int prev = -1;
     cudaGetDevice(&prev);

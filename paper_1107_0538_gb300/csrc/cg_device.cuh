@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "gbcg.h"
+#include "check.cuh"
 #include "layout.h"
 
 namespace gbcg {
@@ -466,7 +467,7 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
         // one long row: the warp reduces it straight from global memory
         AT part = AT(0);
         for (int k = d.a + lane; k < d.e; k += 32)
-            part = fma(to_acc(vals[k], AT(0)), AT(x[P.colidx[k]]), part);
+            part = fma(to_acc(vals[k], AT(0)), AT(x[bchk(P.colidx[k], P.n)]), part);
 #pragma unroll
         for (int mm = 16; mm >= 1; mm >>= 1) part += __shfl_xor_sync(0xffffffffu, part, mm);
         if (lane == 0) epi.row(d.r0, part, j);
@@ -475,18 +476,19 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
         const int32_t *rs = S.rptr<VT, XT>(w) - (d.r0 & ~3);
         const int row = d.r0 + lane;
         if (row < d.r1) {
-            const int k0 = rs[row], k1 = rs[row + 1];
+            int k0 = rs[row], k1 = rs[row + 1];
+            bchk_range(k0, k1, d.a, d.e);
             AT sum = AT(0);
             if (k1 > k0) {
                 if (d.kind == kTileWindow) {
                     const uint16_t *lc = reinterpret_cast<const uint16_t *>(S.cols<VT, XT>(w)) - (d.a & ~7);
                     const XT *win = S.win<VT, XT>(w);
                     sum = row_sum<AT>(k0, k1, [&](int k) { return (int)lc[k]; },
-                                      [&](int c2) { return AT(win[c2]); }, vs);
+                                      [&](int c2) { return AT(win[bchk(c2, kWinMax)]); }, vs);
                 } else {
                     const int32_t *cs = S.cols<VT, XT>(w) - (d.a & ~3);
                     sum = row_sum<AT>(k0, k1, [&](int k) { return cs[k]; },
-                                      [&](int c2) { return AT(x[c2]); }, vs);
+                                      [&](int c2) { return AT(x[bchk(c2, P.n)]); }, vs);
                 }
             }
             epi.row(row, sum, j);

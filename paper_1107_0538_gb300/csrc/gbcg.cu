@@ -539,7 +539,7 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vr[u] = mload(vv + (k + u) * 32, st);
-                    xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
+                    xr[u] = __ldca(x + bchk(row + (int)mload(cc + (k + u) * 32, st), M.n));
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) s = fma(vr[u], xr[u], s);
@@ -550,12 +550,12 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
 #pragma unroll
             for (int u = 0; u < kSellUnroll; ++u) {
                 vr[u] = mload(vv + (k + u) * 32, st);
-                xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
+                xr[u] = __ldca(x + bchk(row + (int)mload(cc + (k + u) * 32, st), M.n));
             }
 #pragma unroll
             for (int u = 0; u < kSellUnroll; ++u) s = fma(vr[u], xr[u], s);
         }
-        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s);
+        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + bchk(row + (int)mload(cc + k * 32, st), M.n)), s);
     } else {
         const int32_t *cc = M.cols32 + a + lane;
         if constexpr (U != kSellUnroll) {
@@ -564,7 +564,7 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     vr[u] = mload(vv + (k + u) * 32, st);
-                    xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
+                    xr[u] = __ldca(x + bchk(mload(cc + (k + u) * 32, st), M.n));
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) s = fma(vr[u], xr[u], s);
@@ -575,12 +575,12 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
 #pragma unroll
             for (int u = 0; u < kSellUnroll; ++u) {
                 vr[u] = mload(vv + (k + u) * 32, st);
-                xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
+                xr[u] = __ldca(x + bchk(mload(cc + (k + u) * 32, st), M.n));
             }
 #pragma unroll
             for (int u = 0; u < kSellUnroll; ++u) s = fma(vr[u], xr[u], s);
         }
-        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + mload(cc + k * 32, st)), s);
+        for (; k < w; ++k) s = fma(mload(vv + k * 32, st), __ldca(x + bchk(mload(cc + k * 32, st), M.n)), s);
     }
     return s;
 }
@@ -1239,7 +1239,7 @@ __device__ __forceinline__ float sell_slice_sum_lo(const SellMatrix &M, const VT
 #pragma unroll
             for (int u = 0; u < kSellUnrollLo; ++u) {
                 vr[u] = lo_load(vv + (k + u) * 32, st);
-                xr[u] = __ldca(x + row + (int)mload(cc + (k + u) * 32, st));
+                xr[u] = __ldca(x + bchk(row + (int)mload(cc + (k + u) * 32, st), M.n));
             }
 #pragma unroll
             for (int u = 0; u < kSellUnrollLo; ++u) {
@@ -1247,7 +1247,7 @@ __device__ __forceinline__ float sell_slice_sum_lo(const SellMatrix &M, const VT
                 else s0 = fmaf(vr[u], xr[u], s0);
             }
         }
-        for (; k < w; ++k) s0 = fmaf(lo_load(vv + k * 32, st), __ldca(x + row + (int)mload(cc + k * 32, st)), s0);
+        for (; k < w; ++k) s0 = fmaf(lo_load(vv + k * 32, st), __ldca(x + bchk(row + (int)mload(cc + k * 32, st), M.n)), s0);
     } else {
         const int32_t *cc = M.cols32 + a + lane;
         for (; k + kSellUnrollLo <= w; k += kSellUnrollLo) {
@@ -1255,7 +1255,7 @@ __device__ __forceinline__ float sell_slice_sum_lo(const SellMatrix &M, const VT
 #pragma unroll
             for (int u = 0; u < kSellUnrollLo; ++u) {
                 vr[u] = lo_load(vv + (k + u) * 32, st);
-                xr[u] = __ldca(x + mload(cc + (k + u) * 32, st));
+                xr[u] = __ldca(x + bchk(mload(cc + (k + u) * 32, st), M.n));
             }
 #pragma unroll
             for (int u = 0; u < kSellUnrollLo; ++u) {
@@ -1263,7 +1263,7 @@ __device__ __forceinline__ float sell_slice_sum_lo(const SellMatrix &M, const VT
                 else s0 = fmaf(vr[u], xr[u], s0);
             }
         }
-        for (; k < w; ++k) s0 = fmaf(lo_load(vv + k * 32, st), __ldca(x + mload(cc + k * 32, st)), s0);
+        for (; k < w; ++k) s0 = fmaf(lo_load(vv + k * 32, st), __ldca(x + bchk(mload(cc + k * 32, st), M.n)), s0);
     }
     return s0 + s1;
 }
@@ -1714,6 +1714,7 @@ const char *cg_strerror(int code) {
 }
 
 int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle **out) {
+    NvtxRange nvtx("gbcg.create");
     if (!out) return CG_EINVAL;
     *out = nullptr;
     if (!A) return CG_EINVAL;
@@ -2080,6 +2081,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
 }
 
 int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    NvtxRange nvtx("gbcg.solve");
     int rc = check_solve_args(h, b, x, tol);
     if (rc != CG_OK) return rc;
     if (h->n == 0) {
@@ -2102,6 +2104,7 @@ int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit
 }
 
 int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    NvtxRange nvtx("gbcg.solve_host");
     int rc = check_solve_args(h, b, x, tol);
     if (rc != CG_OK) return rc;
     if (h->n == 0) {
@@ -2128,6 +2131,7 @@ int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t 
 }
 
 int cg_spmv(cg_handle *h, const double *x, double *y) {
+    NvtxRange nvtx("gbcg.spmv");
     if (!h) return CG_EINVAL;
     if (h->n == 0) return CG_OK;
     if (!x || !y || x == y) return CG_EINVAL;
@@ -2136,6 +2140,7 @@ int cg_spmv(cg_handle *h, const double *x, double *y) {
 }
 
 int cg_spmv_inner(cg_handle *h, const float *x, float *y) {
+    NvtxRange nvtx("gbcg.spmv_inner");
     if (!h || h->opts.inner_values == CG_VALUES_FP64) return CG_EINVAL;
     if (h->n == 0) return CG_OK;
     if (!x || !y) return CG_EINVAL;
@@ -2191,6 +2196,21 @@ int cg_get_plan(const cg_handle *h, cg_plan *plan) {
 }
 
 void cg_destroy(cg_handle *h) { free_handle(h); }
+
+int cg_bounds_faults(int64_t *count) {
+    if (!count) return CG_EINVAL;
+    const long long parts[] = {read_bounds_faults(), bounds_faults_batch(), bounds_faults_learn()};
+    long long tot = 0;
+    for (long long v : parts) {
+        if (v < 0) {
+            *count = -1;
+            return CG_OK;
+        }
+        tot += v;
+    }
+    *count = tot;
+    return CG_OK;
+}
 
 int cg_fp64_peak(void *stream, int32_t iters, double *flops, double *ms) {
     if (iters < 1 || !flops || !ms) return CG_EINVAL;

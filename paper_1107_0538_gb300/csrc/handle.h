@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <vector>
@@ -83,6 +84,15 @@ int dev_alloc(cg_handle *h, T **p, size_t count) {
     return CG_OK;
 }
 
+// An NVTX range over one library call (named "gbcg.<call>"), visible to
+// Nsight tools; without a tool attached it costs a branch.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -110,5 +120,9 @@ int enqueue_spmv(cg_handle *h, const double *x, double *y);
 int learn_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info);
 // Frees the learned-preconditioner workspace of a handle (learn.cu).
 void learn_free(cg_handle *h);
+// Index faults counted by the bounds-check build in batch.cu and learn.cu
+// (-1 in a normal build).
+long long bounds_faults_batch();
+long long bounds_faults_learn();
 
 }  // namespace gbcg

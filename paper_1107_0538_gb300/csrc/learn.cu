@@ -1735,6 +1735,8 @@ int max_ctas(const cg_learn_set *set) {
 
 }  // namespace
 
+long long gbcg::bounds_faults_learn() { return read_bounds_faults(); }
+
 void gbcg::learn_free(cg_handle *h) {
     if (h && h->learn) {
         free_ctx(h->learn);
@@ -1913,6 +1915,7 @@ void cg_net_destroy(cg_net *net) {
 
 int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez, const float *lognu,
                    int32_t stall_window, double stall_factor) {
+    NvtxRange nvtx("gbcg.set_learned");
     if (!h || !net || !lognu || h->opts.precond != CG_PRECOND_LEARNED) return CG_EINVAL;
     if (ex < 1 || ey < 1 || ez < 1) return CG_EINVAL;
     if ((int64_t)(ex + 1) * (ey + 1) * (ez + 1) != (int64_t)h->n) return CG_EINVAL;
@@ -1980,6 +1983,7 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
 }
 
 int cg_precond_apply(cg_handle *h, const double *r, double *z) {
+    NvtxRange nvtx("gbcg.precond_apply");
     if (!h || !h->learn || !r || !z) return CG_EINVAL;
     LearnCtx *L = h->learn;
     DeviceGuard dg(h->device);
@@ -2023,6 +2027,7 @@ int cg_precond_apply(cg_handle *h, const double *r, double *z) {
 
 int cg_learn_pairs(cg_handle *h, const double *b, const double *xstar, int32_t segment, int32_t count,
                    float *r_out, float *e_out) {
+    NvtxRange nvtx("gbcg.learn_pairs");
     if (!h || !h->learn || !b || !xstar || !r_out || !e_out || segment < 1 || count < 1) return CG_EINVAL;
     DeviceGuard dg(h->device);
     LearnCtx *L = h->learn;
@@ -2049,6 +2054,7 @@ int cg_learn_pairs(cg_handle *h, const double *b, const double *xstar, int32_t s
 
 int cg_learn_grad(cg_net *net, const cg_learn_set *set, const int64_t *pairs, int32_t count, double *loss,
                   float *grad) {
+    NvtxRange nvtx("gbcg.learn_grad");
     int rc = check_set(net, set);
     if (rc != CG_OK) return rc;
     if (!pairs || count < 1 || !loss) return CG_EINVAL;
@@ -2088,6 +2094,7 @@ int cg_learn_grad(cg_net *net, const cg_learn_set *set, const int64_t *pairs, in
 
 int cg_learn_train(cg_net *net, const cg_learn_set *set, const int64_t *order, int32_t steps, int32_t batch,
                    float lr, double *losses) {
+    NvtxRange nvtx("gbcg.learn_train");
     int rc = check_set(net, set);
     if (rc != CG_OK) return rc;
     if (!order || steps < 1 || batch < 1 || !(lr > 0.0f) || !std::isfinite(lr)) return CG_EINVAL;

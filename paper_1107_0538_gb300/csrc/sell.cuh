@@ -17,6 +17,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "check.cuh"
+
 namespace gbcg {
 
 struct SellMatrix {
@@ -64,7 +66,7 @@ __device__ __forceinline__ void sell_rows(const SellMatrix &M, const double *__r
 #pragma unroll
                 for (int u = 0; u < kSellUnroll; ++u) {
                     vr[u] = mload(vv + (k + u) * 32, st);
-                    xr[u] = __ldg(x + row + (int)mload(cc + (k + u) * 32, st));
+                    xr[u] = __ldg(x + bchk(row + (int)mload(cc + (k + u) * 32, st), M.n));
                 }
 #pragma unroll
                 for (int u = 0; u < kSellUnroll; ++u) {
@@ -72,7 +74,7 @@ __device__ __forceinline__ void sell_rows(const SellMatrix &M, const double *__r
                     else s0 = fma(vr[u], xr[u], s0);
                 }
             }
-            for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldg(x + row + (int)mload(cc + k * 32, st)), s0);
+            for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldg(x + bchk(row + (int)mload(cc + k * 32, st), M.n)), s0);
         } else {
             const int32_t *cc = M.cols32 + a + lane;
             for (; k + kSellUnroll <= w; k += kSellUnroll) {
@@ -80,7 +82,7 @@ __device__ __forceinline__ void sell_rows(const SellMatrix &M, const double *__r
 #pragma unroll
                 for (int u = 0; u < kSellUnroll; ++u) {
                     vr[u] = mload(vv + (k + u) * 32, st);
-                    xr[u] = __ldg(x + mload(cc + (k + u) * 32, st));
+                    xr[u] = __ldg(x + bchk(mload(cc + (k + u) * 32, st), M.n));
                 }
 #pragma unroll
                 for (int u = 0; u < kSellUnroll; ++u) {
@@ -88,7 +90,7 @@ __device__ __forceinline__ void sell_rows(const SellMatrix &M, const double *__r
                     else s0 = fma(vr[u], xr[u], s0);
                 }
             }
-            for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldg(x + mload(cc + k * 32, st)), s0);
+            for (; k < w; ++k) s0 = fma(mload(vv + k * 32, st), __ldg(x + bchk(mload(cc + k * 32, st), M.n)), s0);
         }
         if (row < M.n) epi.row(row, s0 + s1, 0);
     }

@@ -18,7 +18,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgbcg.so")
+# GBCG_LIBRARY=check loads the bounds-check build (libgbcg_check.so) instead.
+LIB_PATH = os.path.join(_HERE, "libgbcg_check.so" if os.environ.get("GBCG_LIBRARY") == "check" else "libgbcg.so")
 
 CG_OK, CG_EINVAL, CG_ENOMEM, CG_ECUDA = 0, 1, 2, 3
 CG_ENOCONV, CG_EBREAKDOWN, CG_ENAN, CG_ETIMEOUT = 4, 5, 6, 7
@@ -28,7 +29,7 @@ CG_VALUES_FP64, CG_VALUES_FP32, CG_VALUES_BF16 = 0, 1, 2
 
 # Every entry point of include/gbcg.h (checked against the header by the tests).
 EXPORTS = ("cg_version", "cg_opts_default", "cg_create", "cg_solve", "cg_solve_host",
-           "cg_spmv", "cg_spmv_inner", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_fp64_peak",
+           "cg_spmv", "cg_spmv_inner", "cg_get_plan", "cg_destroy", "cg_strerror", "cg_bounds_faults", "cg_fp64_peak",
            "cg_solve_noalloc",
            "cg_batch_create", "cg_batch_enqueue", "cg_batch_results", "cg_batch_solve",
            "cg_batch_tune", "cg_batch_set_tuning", "cg_batch_destroy", "cg_net_create", "cg_net_get_params",
@@ -131,6 +132,8 @@ def lib() -> ctypes.CDLL:
             L.cg_destroy.restype = None
             L.cg_strerror.argtypes = [ctypes.c_int]
             L.cg_strerror.restype = ctypes.c_char_p
+            L.cg_bounds_faults.argtypes = [ctypes.POINTER(ctypes.c_int64)]
+            L.cg_bounds_faults.restype = ctypes.c_int
             L.cg_fp64_peak.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
             L.cg_fp64_peak.restype = ctypes.c_int
             L.cg_solve_noalloc.argtypes = [ctypes.POINTER(cg_csr), vp, vp, dbl, i32, vp,
@@ -234,6 +237,15 @@ def cg_destroy(h: int | None) -> None:
 
 def cg_strerror(code: int) -> str:
     return lib().cg_strerror(int(code)).decode()
+
+
+def cg_bounds_faults() -> int:
+    """Index faults counted by the bounds-check build (-1: a normal build)."""
+    c = ctypes.c_int64(0)
+    rc = lib().cg_bounds_faults(ctypes.byref(c))
+    if rc != CG_OK:
+        raise GbcgError(rc, "cg_bounds_faults")
+    return int(c.value)
 
 
 def cg_fp64_peak(stream: int | None, iters: int) -> tuple[int, float, float]:
