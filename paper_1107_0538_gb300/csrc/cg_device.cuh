@@ -448,6 +448,16 @@ __device__ __forceinline__ AT row_sum(int k0, int k1, const Col &col_of, const V
     return s0 + s1;
 }
 
+// Epilogues that read vector entries of their row may define prefetch(i):
+// it is called with the lane's row before the wait for the tile's stage, so
+// those loads overlap the wait and the row sum instead of following it.
+template <class E>
+__device__ __forceinline__ auto maybe_prefetch(E &e, int i, int) -> decltype(e.prefetch(i), void()) {
+    e.prefetch(i);
+}
+template <class E>
+__device__ __forceinline__ void maybe_prefetch(E &, int, long) {}
+
 // One tile of a warp: waits for its stage, forms the row sums and calls
 // epi.row(i, sum, j) for each row i of the tile (lane l gets row r0 + l; j is
 // the warp's local tile number in the pass).  Returns false if the wait ran
@@ -460,6 +470,10 @@ __device__ __forceinline__ bool warp_tile(const Params &P, const Smem &S, Pipe &
     const uint32_t c = pp.consumed;
     const TileDesc d = load_desc(P, t0 + w + kWarps * (int)(c % (uint32_t)m));
     store_tail<VT, XT>(P, S, d, w, x);  // nobody reads the stage before the wait below
+    {
+        const int prow = d.kind == kTileLong ? d.r0 : d.r0 + lane;
+        if (prow < d.r1) maybe_prefetch(epi, prow, 0);
+    }
     const bool got = mbar_wait_bounded(&S.mbar[w], c & 1u, P.wait_ns);
     if (__any_sync(0xffffffffu, !got)) return false;
     __syncwarp();

@@ -114,9 +114,15 @@ struct EpiIter {        // p = z + beta p, q = A z + beta q; sum p . q
     const double *z;    // the gathered vector (own rows read back)
     double beta;
     double pq = 0.0;
+    double zi_ = 0.0, qi_ = 0.0, pi_ = 0.0;   // the row's entries, loaded ahead
+    __device__ __forceinline__ void prefetch(int i) {
+        zi_ = z[i];
+        qi_ = q[i];
+        pi_ = pd[i];
+    }
     __device__ __forceinline__ void row(int i, double az, int) {
-        const double qi = fma(beta, q[i], az);
-        const double pi = fma(beta, pd[i], z[i]);
+        const double qi = fma(beta, qi_, az);
+        const double pi = fma(beta, pi_, zi_);
         q[i] = qi;
         pd[i] = pi;
         pq = fma(pi, qi, pq);
@@ -1053,10 +1059,16 @@ struct EpiInner {       // p = z + beta p, q = A_lo z + beta q (A_lo with its co
     const float *diag;
     float beta;
     float pq = 0.0f;
+    float zi_ = 0.0f, qi_ = 0.0f, pi_ = 0.0f, di_ = 0.0f;   // the row's entries, loaded ahead
+    __device__ __forceinline__ void prefetch(int i) {
+        zi_ = z32[i];
+        qi_ = q32[i];
+        pi_ = pd32[i];
+        di_ = __ldg(diag + i);
+    }
     __device__ __forceinline__ void row(int i, float s, int) {
-        const float zi = z32[i];
-        const float qi = fmaf(beta, q32[i], fmaf(diag[i], zi, s));
-        const float pi = fmaf(beta, pd32[i], zi);
+        const float qi = fmaf(beta, qi_, fmaf(di_, zi_, s));
+        const float pi = fmaf(beta, pi_, zi_);
         q32[i] = qi;
         pd32[i] = pi;
         pq = fmaf(pi, qi, pq);
@@ -1144,17 +1156,36 @@ __global__ void __launch_bounds__(kThreads, 1) cg_ir_kernel(Params P) {
             if (!S.ctl[kCtlRun]) break;
             const float alpha = (float)S.bcast[2];
             float prr = 0.0f, prz = 0.0f;
-            for (int i = row_lo + tid; i < row_hi; i += kThreads) {
-                P.d32[i] = fmaf(alpha, P.pd32[i], P.d32[i]);
-                const float ri = fmaf(-alpha, P.q32[i], P.r32[i]);
-                P.r32[i] = ri;
-                prr = fmaf(ri, ri, prr);
-                float zi = ri;
-                if (P.precond) {
-                    zi = P.dinv32[i] * ri;
-                    prz = fmaf(ri, zi, prz);
+            // four rows per thread at a time: every load of the four is issued
+            // before the first store (the arrays do not alias)
+            constexpr int kU = 4;
+            for (int i0 = row_lo + tid; i0 < row_hi; i0 += kU * kThreads) {
+                float pv[kU], qv[kU], dv[kU], rv[kU], iv[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int i = i0 + u * kThreads;
+                    const bool in = i < row_hi;
+                    pv[u] = in ? P.pd32[i] : 0.0f;
+                    qv[u] = in ? P.q32[i] : 0.0f;
+                    dv[u] = in ? P.d32[i] : 0.0f;
+                    rv[u] = in ? P.r32[i] : 0.0f;
+                    iv[u] = in && P.precond ? __ldg(P.dinv32 + i) : 1.0f;
                 }
-                P.p32[i] = zi;   // gathered by the next SpMV (every gather of this one is over)
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int i = i0 + u * kThreads;
+                    if (i >= row_hi) break;
+                    P.d32[i] = fmaf(alpha, pv[u], dv[u]);
+                    const float ri = fmaf(-alpha, qv[u], rv[u]);
+                    P.r32[i] = ri;
+                    prr = fmaf(ri, ri, prr);
+                    float zi = ri;
+                    if (P.precond) {
+                        zi = iv[u] * ri;
+                        prz = fmaf(ri, zi, prz);
+                    }
+                    P.p32[i] = zi;   // gathered by the next SpMV (every gather of this one is over)
+                }
             }
             double v2[2] = {(double)prr, (double)(P.precond ? prz : prr)};
             block_sum<2>(v2, S);

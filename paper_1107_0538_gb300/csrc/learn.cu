@@ -897,9 +897,11 @@ struct EpiQ {           // q = A p; p.q
     const double *p;
     double *q;
     double pq = 0.0;
+    double pi_ = 0.0;   // the row's entry of p, loaded ahead
+    __device__ __forceinline__ void prefetch(int i) { pi_ = p[i]; }
     __device__ __forceinline__ void row(int i, double aq, int) {
         q[i] = aq;
-        pq = fma(p[i], aq, pq);
+        pq = fma(pi_, aq, pq);
     }
 };
 struct EpiTrueL {       // ||b - A x||^2
