@@ -44,12 +44,13 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 100^3 SpMV roofline, the other forms, the batch and the CPU baseline")
     ap.add_argument("--section", choices=["spmv", "forms", "forms100", "batched", "batched_small", "learned",
-                                          "learned_iter", "fp64peak"],
+                                          "learned_iter", "learned_iter100", "fp64peak"],
                     help="run one extra section alone and print its JSON: the 100^3 SpMV roofline, the "
                          "other forms on the 50^3 workload, the forms on the 100^3 system, "
                          "the 256-system batch (edges 20..80), a 64-system batch (edges 20..40), "
                          "the learned preconditioner (training and tests), the time per flexible-CG "
-                         "iteration with an untrained network at 50^3 and 100^3, or the FP64 peak probe")
+                         "iteration with an untrained network at 50^3 and 100^3 (or 100^3 alone), or the "
+                         "FP64 peak probe")
     ap.add_argument("--batched-full", action="store_true", help="same as --section batched")
     ap.add_argument("--learned-only", action="store_true", help="same as --section learned")
     return ap.parse_args()
@@ -643,7 +644,7 @@ def measure_spmv_hbm(peaks: dict, flush, fp64_tflops: float) -> dict:
     }
 
 
-def measure_learned_iter(maxits=(12, 36)) -> dict:
+def measure_learned_iter(maxits=(12, 36), grids=(50, 100)) -> dict:
     """ms per flexible-CG iteration with the untrained network (the cost of an
     iteration does not depend on the weights): the slope between maxit = 12 and
     36 on the 50^3 workload grid and on a 100^3 instance."""
@@ -653,7 +654,7 @@ def measure_learned_iter(maxits=(12, 36)) -> dict:
     dev = torch.device("cuda", torch.cuda.current_device())
     net = gbcg.Net(problems.learn_init_params())
     out = {}
-    for e in (50, 100):
+    for e in grids:
         inst = problems.learn_instance(e, 20001)
         s = gbcg.Solver(inst.A, precond=gbcg.CG_PRECOND_LEARNED, true_residual=False)
         s.set_learned(net, inst.grid, inst.lognu.astype(np.float32))
@@ -702,6 +703,8 @@ def run_section(args) -> None:
         out = fp64_peak(torch.cuda.current_stream())
     elif name == "learned_iter":
         out = measure_learned_iter()
+    elif name == "learned_iter100":
+        out = measure_learned_iter(grids=(100,))
     else:
         out = measure_learned()
     print(json.dumps({"section": name, name: out}), flush=True)

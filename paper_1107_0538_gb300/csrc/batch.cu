@@ -192,6 +192,16 @@ __device__ __forceinline__ T system_total(const BatchParams &B, int set, int sys
     return s;
 }
 
+// Row functions that read their row's vector entries may define
+// prefetch(row): with one lane per row it is called for the lane's row before
+// the wait for the tile's stage, so those loads overlap the wait and the sum.
+template <class F>
+__device__ __forceinline__ auto batch_prefetch(F &f, int i, int) -> decltype(f.prefetch(i), void()) {
+    f.prefetch(i);
+}
+template <class F>
+__device__ __forceinline__ void batch_prefetch(F &, int, long) {}
+
 template <class VT, class XT, class AT, class Active, class RowFn, class Acc>
 __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, uint32_t &count,
                                            const VT *vals, const XT *x, const Active &active, RowFn &rowfn,
@@ -229,6 +239,7 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
             const TileDesc d = load_desc(P, cur);
             const int sys = B.tile_sys[cur];
             store_tail<VT, XT>(P, S, d, w, x);
+            if (B.lanes_per_row == 1 && d.kind != kTileLong && d.r0 + lane < d.r1) batch_prefetch(rowfn, d.r0 + lane, 0);
             const bool got = mbar_wait_bounded(&S.mbar[w], count & 1u, P.wait_ns);
             if (__any_sync(0xffffffffu, !got)) {
                 ok = false;
@@ -289,6 +300,42 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
     return ok;
 }
 
+
+// Row function of the inner SpMM pass: p = z + beta p, q = A_lo z + beta q
+// (= A_lo p) for the four right-hand sides of row i, p.q per right-hand side.
+// With one lane per row the row's z, q, p and diagonal are loaded ahead
+// (prefetch), before the tile's stage is waited for.
+struct SpmmRow {
+    const BatchParams &B;
+    const PairState *st;
+    int pi = -1;                 // row whose entries were loaded ahead
+    float4 pz, pq, pp;
+    float pdg;
+    __device__ __forceinline__ void prefetch(int i) {
+        pi = i;
+        pz = B.p32[i];
+        pq = B.q32[i];
+        pp = B.pd32[i];
+        pdg = B.P.diag_lo[i];
+    }
+    __device__ __forceinline__ void operator()(int sys, int i, float4 s4, WarpAcc<float, 4> &a) {
+        const PairState *ps = st + sys * kRhs;
+        const float b0 = ps[0].beta, b1 = ps[1].beta, b2 = ps[2].beta, b3 = ps[3].beta;
+        const bool ahead = pi == i;
+        const float dg = ahead ? pdg : B.P.diag_lo[i];
+        const float4 z = ahead ? pz : B.p32[i], q0 = ahead ? pq : B.q32[i], p0 = ahead ? pp : B.pd32[i];
+        const float4 qv = make_float4(fmaf(b0, q0.x, fmaf(dg, z.x, s4.x)), fmaf(b1, q0.y, fmaf(dg, z.y, s4.y)),
+                                      fmaf(b2, q0.z, fmaf(dg, z.z, s4.z)), fmaf(b3, q0.w, fmaf(dg, z.w, s4.w)));
+        const float4 p = make_float4(fmaf(b0, p0.x, z.x), fmaf(b1, p0.y, z.y), fmaf(b2, p0.z, z.z),
+                                     fmaf(b3, p0.w, z.w));
+        B.q32[i] = qv;
+        B.pd32[i] = p;
+        a.a[0] = fmaf(p.x, qv.x, a.a[0]);
+        a.a[1] = fmaf(p.y, qv.y, a.a[1]);
+        a.a[2] = fmaf(p.z, qv.z, a.a[2]);
+        a.a[3] = fmaf(p.w, qv.w, a.a[3]);
+    }
+};
 
 // ---------------------------------------------------------------- kernel
 template <class VT>
@@ -409,24 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     {
                         WarpAcc<float, 4> acc;
                         acc.seg = -1;
-                        auto rowfn = [&](int sys, int i, float4 s4, WarpAcc<float, 4> &a) {
-                            const PairState *pp = st + sys * kRhs;
-                            const float b0 = pp[0].beta, b1 = pp[1].beta, b2 = pp[2].beta, b3 = pp[3].beta;
-                            const float dg = P.diag_lo[i];
-                            const float4 z = B.p32[i], q0 = B.q32[i], p0 = B.pd32[i];
-                            const float4 qv = make_float4(fmaf(b0, q0.x, fmaf(dg, z.x, s4.x)),
-                                                          fmaf(b1, q0.y, fmaf(dg, z.y, s4.y)),
-                                                          fmaf(b2, q0.z, fmaf(dg, z.z, s4.z)),
-                                                          fmaf(b3, q0.w, fmaf(dg, z.w, s4.w)));
-                            const float4 p = make_float4(fmaf(b0, p0.x, z.x), fmaf(b1, p0.y, z.y),
-                                                         fmaf(b2, p0.z, z.z), fmaf(b3, p0.w, z.w));
-                            B.q32[i] = qv;
-                            B.pd32[i] = p;
-                            a.a[0] = fmaf(p.x, qv.x, a.a[0]);
-                            a.a[1] = fmaf(p.y, qv.y, a.a[1]);
-                            a.a[2] = fmaf(p.z, qv.z, a.a[2]);
-                            a.a[3] = fmaf(p.w, qv.w, a.a[3]);
-                        };
+                        SpmmRow rowfn{B, st};
                         if (!batch_pass<VT, float4, float4>(B, S, count, vlo, B.p32, active, rowfn, acc)) goto out;
                     }
                     combine_segments(B, set, 4);
