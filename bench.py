@@ -76,7 +76,7 @@ def fp64_peak(stream) -> dict:
     import torch
 
     from paper_1107_0538_gb300 import gbcg
-    rc, flops, ms = gbcg.cg_fp64_peak(stream.cuda_stream, 20000)
+    rc, flops, ms = gbcg.cg_fp64_peak(stream.cuda_stream, 4000)
     if rc != gbcg.CG_OK or ms <= 0:
         raise RuntimeError(f"cg_fp64_peak failed: {gbcg.cg_strerror(rc)}")
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count

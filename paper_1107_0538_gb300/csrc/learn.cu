@@ -20,9 +20,10 @@
 // past the grid (ragged bricks) are computed and dropped, so every store
 // goes to an interior node and the zero halo is never overwritten.
 //
-// Flexible CG runs as a CUDA graph of kUnroll iterations of seven kernels
-// (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, p update, SpMV + p.q,
-// x/r update + stop test); scalars are decided by the last CTA to finish each
+// Flexible CG runs as a CUDA graph of kUnroll iterations of six kernels
+// (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, SpMV of z with the
+// p = z + beta p and q = A z + beta q updates + p.q, x/r update + stop
+// test); scalars are decided by the last CTA to finish each
 // reducing kernel (fixed-order sums: bitwise reproducible) and kept in a
 // device state block; kernels return at once after the solve is done.
 #include <cuda_bf16.h>
@@ -235,6 +236,7 @@ struct ConvArgs {
     Geo G;
     const __nv_bfloat16 *in;     // padded input (16 channels, or 1 channel for conv1)
     const double *dsq;           // 1 / sqrt(diag A)
+    const float *dsq32;          // the same in FP32 (E_OUT_Z, E_OUT_FCG: z = sigma D^-1/2 u in FP32)
     const __nv_bfloat16 *w;      // packed weights of this convolution
     const float *bias;           // E_SIGMOID
     __nv_bfloat16 *out;          // padded 16-channel output
@@ -645,6 +647,27 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double *sred) {
     __syncthreads();
 }
 
+// Sums two values over a CTA of 256 threads and gives the totals to every
+// thread.  The values are parked in shared memory (`park`, 512 doubles) and
+// value j is added by warp j, 8 entries per lane as a depth-3 tree and then a
+// butterfly: the FP64 adds (64 cycles of an SM sub-partition per warp
+// instruction on GB300) run on two warps instead of all eight.  Fixed order.
+__device__ __forceinline__ void cta_sum2_256(double (&v)[2], double *park, double *sred) {
+    park[threadIdx.x] = v[0];
+    park[256 + threadIdx.x] = v[1];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < 2) {
+        const double *q = park + 256 * w + lane;
+        double t = ((q[0] + q[32]) + (q[64] + q[96])) + ((q[128] + q[160]) + (q[192] + q[224]));
+        t = warp_sum(t);
+        if (lane == 0) sred[w] = t;
+    }
+    __syncthreads();
+    v[0] = sred[0];
+    v[1] = sred[1];
+}
+
 // Publishes this CTA's partials (thread 0 holds them); true in every thread
 // of the last CTA to arrive, which then sums all partials into tot (warp 0)
 // and resets the counter.  Every thread of that CTA adds a fixed strided
@@ -696,7 +719,7 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double sred[2 * 32];
     __shared__ float su[kRows * kBX];
-    __shared__ int sflag;
+    __shared__ int sflag, sswitch;
     const Geo &G = A.G;
     const bool learned = !st || st->mode == kModeLearned;
     double dzr = 0.0, dzq = 0.0;
@@ -740,7 +763,9 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
                     su[((w >> 1) * kBY + 4 * (w & 1) + m) * kBX + g + 8 * hr] = acc[m][2 * hr];
         }
         __syncthreads();
-        const double sigma = EPI == E_OUT_U ? 1.0 : (st ? st->sigma : A.sigma[0]);
+        // z = sigma D^-1/2 u in FP32 (u is the output of BF16 products; FP32
+        // adds nothing to its error), widened for the FP64 dot products
+        const float sigma = EPI == E_OUT_U ? 1.0f : (float)(st ? st->sigma : A.sigma[0]);
         for (int idx = threadIdx.x; idx < kRows * kBX; idx += blockDim.x) {
             const int row = idx / kBX, xr = idx - row * kBX;
             const int x = B.x0 + xr, y = B.y0 + row % kBY, z = B.z0 + row / kBY;
@@ -750,7 +775,7 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
             if (EPI == E_OUT_U) {
                 A.u[i] = u;
             } else {
-                const double zi = sigma * A.dsq[i] * (double)u;
+                const double zi = (double)(sigma * A.dsq32[i] * u);
                 A.z[i] = zi;
                 if (EPI == E_OUT_FCG) {
                     dzr = fma(zi, A.r[i], dzr);
@@ -769,8 +794,10 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     }
     if (EPI != E_OUT_FCG) return;
     double v[2] = {dzr, dzq}, tot[2];
-    cta_sum<2>(v, sred);
+    __syncthreads();   // the staged input (learned mode) is dead: its space holds the parked sums
+    cta_sum2_256(v, reinterpret_cast<double *>(sm), sred);
     if (!last_cta_totals<2>(v, A.partials, &st->counter, tot, &sflag, sred)) return;
+    if (threadIdx.x == 0) sswitch = 0;
     if (threadIdx.x == 0) {
         const double zr = tot[0], zq = tot[1];
         st->zr = zr;
@@ -783,6 +810,7 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
             st->restart = 2;
             st->rho = st->rdr;
             st->beta = 0.0;
+            sswitch = 1;
         } else if (!finite_bits(zr)) {
             finish(st, CG_ENAN);
         } else if (!(zr > 0.0)) {
@@ -792,6 +820,11 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
             st->rho = zr;
         }
     }
+    // on the switch the next SpMV gathers z = D^-1 r (the Jacobi direction),
+    // not the network's output: this CTA rewrites z (once per solve at most)
+    __syncthreads();
+    if (sswitch)
+        for (int i = threadIdx.x; i < G.n; i += blockDim.x) A.z[i] = A.dinv[i] * A.r[i];
 }
 
 // ------------------------------------------------------- vector kernels
@@ -800,43 +833,37 @@ struct VecArgs {
     FcgState *st;
     double *x, *r, *z, *p, *q;
     const double *dinv, *dsq;
+    const float *dsq32;       // D^-1/2 in FP32 (the network input s = D^-1/2 r)
     const int32_t *pidx;      // padded position of each node
     __nv_bfloat16 *s_in;      // padded network input D^-1/2 r (BF16)
     double *partials;
 };
 
-// p = z + beta p (p = z after a restart; p = D^-1 r after a switch to Jacobi).
-__global__ void __launch_bounds__(kVT) fcg_p_kernel(VecArgs V) {
-    const FcgState *st = V.st;
-    if (st->done) return;
-    const int restart = st->restart;
-    const double beta = st->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x) {
-        if (restart == 2) V.p[i] = V.dinv[i] * V.r[i];
-        else if (restart == 1) V.p[i] = V.z[i];
-        else V.p[i] = fma(beta, V.p[i], V.z[i]);
-    }
-}
-
 // x += alpha p, r -= alpha q; r.r and r.D^-1 r; stop test, stall test.
+// The network input s = D^-1/2 r and r.D^-1 r = s.s are formed in FP32 (s is
+// stored in BF16; r.D^-1 r only scales the network input, and after a
+// switch to Jacobi-PCG it is the first rho); x, r and r.r stay FP64.
 __global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
     FcgState *st = V.st;
     if (st->done) return;
     __shared__ double sred[2 * 32];
+    __shared__ double park[2 * kVT];
     __shared__ int sflag;
     const double alpha = st->alpha;
     double *x = st->x;
-    double rr = 0.0, rdr = 0.0;
+    double rr = 0.0;
+    float rdr = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x) {
         x[i] = fma(alpha, V.p[i], x[i]);
         const double ri = fma(-alpha, V.q[i], V.r[i]);
         V.r[i] = ri;
-        V.s_in[V.pidx[i]] = __float2bfloat16_rn((float)(ri * V.dsq[i]));
+        const float si = (float)ri * V.dsq32[i];
+        V.s_in[V.pidx[i]] = __float2bfloat16_rn(si);
         rr = fma(ri, ri, rr);
-        rdr = fma(ri * V.dinv[i], ri, rdr);
+        rdr = fmaf(si, si, rdr);
     }
-    double v[2] = {rr, rdr}, tot[2];
-    cta_sum<2>(v, sred);
+    double v[2] = {rr, (double)rdr}, tot[2];
+    cta_sum2_256(v, park, sred);
     if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag, sred)) return;
     // warp 0 of the last CTA: the residual-norm window for the stall test
     const int lane = threadIdx.x & 31;
@@ -893,15 +920,24 @@ struct EpiSetupL {      // r = b - A x, s_in = D^-1/2 r; r.r, b.b, r.D^-1 r
         rdr = fma(ri * dinv[i], ri, rdr);
     }
 };
-struct EpiQ {           // q = A p; p.q
-    const double *p;
+struct EpiQ {           // p = z + beta p, q = A z + beta q (= A p); p.q
+    const double *z;    // the gathered vector
+    double *p;
     double *q;
+    double beta;        // 0 after a restart (p = z)
     double pq = 0.0;
-    double pi_ = 0.0;   // the row's entry of p, loaded ahead
-    __device__ __forceinline__ void prefetch(int i) { pi_ = p[i]; }
-    __device__ __forceinline__ void row(int i, double aq, int) {
-        q[i] = aq;
-        pq = fma(pi_, aq, pq);
+    double zi_ = 0.0, pi_ = 0.0, qi_ = 0.0;   // the row's entries, loaded ahead
+    __device__ __forceinline__ void prefetch(int i) {
+        zi_ = z[i];
+        pi_ = p[i];
+        qi_ = q[i];
+    }
+    __device__ __forceinline__ void row(int i, double az, int) {
+        const double qi = fma(beta, qi_, az);
+        const double pi = fma(beta, pi_, zi_);
+        q[i] = qi;
+        p[i] = pi;
+        pq = fma(pi, qi, pq);
     }
 };
 struct EpiTrueL {       // ||b - A x||^2
@@ -937,7 +973,7 @@ __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgStat
         v[1] = e.bb;
         v[2] = e.rdr;
     } else if (MODE == S_Q) {
-        EpiQ e{vec, P.q};
+        EpiQ e{vec, V.p, P.q, st->restart ? 0.0 : st->beta};
         (void)spmv_tiles<0, double, double, double>(P, S, pipe, P.vals, vec, e, true);
         v[0] = e.pq;
     } else {
@@ -1315,8 +1351,11 @@ __global__ void __launch_bounds__(kVT) scatter_s_kernel(int n, const double *r, 
         s_in[pidx[i]] = __float2bfloat16_rn((float)(r[i] * dsq[i]));
 }
 
-__global__ void __launch_bounds__(kVT) dsq_kernel(int n, const double *dinv, double *dsq) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dsq[i] = sqrt(dinv[i]);
+__global__ void __launch_bounds__(kVT) dsq_kernel(int n, const double *dinv, double *dsq, float *dsq32) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        dsq[i] = sqrt(dinv[i]);
+        dsq32[i] = (float)dsq[i];
+    }
 }
 
 }  // namespace
@@ -1355,6 +1394,7 @@ struct LearnCtx {
     __nv_bfloat16 *s_in = nullptr;   // padded D^-1/2 r (network input)
     int32_t *pidx = nullptr;         // padded position of each node
     double *dsq = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    float *dsq32 = nullptr;          // D^-1/2 in FP32
     double *partials = nullptr, *sigma = nullptr;
     unsigned int *counter = nullptr;
     int *conv_err = nullptr;         // timeout report of the tensor-core convolution (apply)
@@ -1480,19 +1520,21 @@ VecArgs vec_args(cg_handle *h, LearnCtx *L) {
     V.q = L->q;
     V.dinv = h->dinv;
     V.dsq = L->dsq;
+    V.dsq32 = L->dsq32;
     V.pidx = L->pidx;
     V.s_in = L->s_in;
     V.partials = L->partials;
     return V;
 }
 
-// One flexible-CG iteration: seven launches.
+// One flexible-CG iteration: six launches.
 void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     const Geo &G = L->G;
     const cg_net *net = L->net;
     ConvArgs A = conv_args(G);
     A.st = L->st;
     A.dsq = L->dsq;
+    A.dsq32 = L->dsq32;
     A.gate = L->gates;
     // h1 = g * C1(D^-1/2 r) / sigma
     A.in = L->s_in;
@@ -1520,8 +1562,8 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.partials = L->partials;
     convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
     const VecArgs V = vec_args(h, L);
-    fcg_p_kernel<<<L->vgrid, kVT, 0, s>>>(V);
-    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, L->p, L->partials, V);
+    // p = z + beta p and q = A z + beta q in the SpMV's epilogue (it gathers z)
+    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, L->z, L->partials, V);
     fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
 }
 
@@ -1750,7 +1792,6 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
     LearnCtx *L = h->learn;
     if (!L || !L->net) return CG_EINVAL;
     cg_net *net = L->net;
-    const Geo &G = L->G;
     cudaStream_t s = h->stream;
     const size_t bytes = sizeof(double) * (size_t)h->n;
     int rc = set_smem_limits();
@@ -1952,7 +1993,8 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
         (rc = ctx_alloc(A, &L->s_in, act_count(G, 1))) || (rc = ctx_alloc(A, &L->pidx, (size_t)G.n)) ||
         (rc = ctx_alloc(A, &L->h1, a16)) || (rc = ctx_alloc(A, &L->h2, a16)) || (rc = ctx_alloc(A, &L->k1, a16)) ||
         (rc = ctx_alloc(A, &L->dsq, (size_t)G.n)) || (rc = ctx_alloc(A, &L->r, (size_t)G.n)) ||
-        (rc = ctx_alloc(A, &L->z, (size_t)G.n)) || (rc = ctx_alloc(A, &L->p, (size_t)G.n + 16)) ||
+        (rc = ctx_alloc(A, &L->z, (size_t)G.n + 16)) || (rc = ctx_alloc(A, &L->p, (size_t)G.n + 16)) ||
+        (rc = ctx_alloc(A, &L->dsq32, (size_t)G.n)) ||
         (rc = ctx_alloc(A, &L->q, (size_t)G.n)) || (rc = ctx_alloc(A, &L->partials, (size_t)3 * nparts)) ||
         (rc = ctx_alloc(A, &L->sigma, 4)) || (rc = ctx_alloc(A, &L->counter, 4)) || (rc = ctx_alloc(A, &L->st, 1)) ||
         (rc = ctx_alloc(A, &L->dst, 1)) || (rc = ctx_alloc(A, &L->conv_err, 1)))
@@ -1978,7 +2020,7 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
     if (cudaMemcpy(L->lognu_in, ln.data(), ln.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(L->pidx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(CG_ECUDA);
-    dsq_kernel<<<L->vgrid, kVT, 0, h->stream>>>(G.n, h->dinv, L->dsq);
+    dsq_kernel<<<L->vgrid, kVT, 0, h->stream>>>(G.n, h->dinv, L->dsq, L->dsq32);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(CG_ECUDA);
     h->learn = L;
     return CG_OK;
@@ -1999,6 +2041,7 @@ int cg_precond_apply(cg_handle *h, const double *r, double *z) {
     scatter_s_kernel<<<L->vgrid, kVT, 0, s>>>(G.n, r, L->dsq, L->pidx, L->s_in);
     ConvArgs A = conv_args(G);
     A.dsq = L->dsq;
+    A.dsq32 = L->dsq32;
     A.gate = L->gates;
     A.sigma = L->sigma;
     A.in = L->s_in;
