@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         }
         block_sum_1k<3>(v, red, quarter);
         publish_partials<3>(P, set, v);
-        if (!grid_barrier(P, epoch, S)) goto out;
+        if (!grid_barrier<false>(P, epoch, S)) goto out;
         double tot[3];
         grid_totals_1k<3>(P, set, tot, quarter);
         set ^= 1;
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<1>(v1, red, quarter);
             publish_partials<1>(P, set, v1);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double sg[1];
             grid_totals_1k<1>(P, set, sg, quarter);
             set ^= 1;
@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
                 if (own) x = fma(alpha, p, x);
                 azl = sell_slice_sum(M, t, zg, 0.0, 0, wl);
             } else if (tid == 0) {
-                ctl[15] = grid_wait(P, epoch);
+                ctl[15] = grid_wait<false>(P, epoch);
             }
             __syncthreads();
             if (!ctl[15]) goto out;
@@ -784,7 +784,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         const bool want_true = ctl[kCtlTrue] != 0;
         if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
         if (want_true) {
-            if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
+            if (!grid_barrier<false>(P, epoch, S)) goto out;  // every x entry is written
             const double ax = has_slice ? sell_slice_sum(M, t, P.x, 0.0) : 0.0;
             double v[1] = {0.0};
             if (own) {
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<1>(v, red, quarter);
             publish_partials<1>(P, set, v);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double tt[1];
             grid_totals_1k<1>(P, set, tt, quarter);
             if (tid == 0) true_rr = tt[0];
@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         }
         block_sum_1k<3>(v, red, quarter);
         publish_partials<3>(P, set, v);
-        if (!grid_barrier(P, epoch, S)) goto out;
+        if (!grid_barrier<false>(P, epoch, S)) goto out;
         double tot[3];
         grid_totals_1k<3>(P, set, tot, quarter);
         set ^= 1;
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<1>(v1, red, quarter);
             publish_partials<1>(P, set, v1);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double sg[1];
             grid_totals_1k<1>(P, set, sg, quarter);
             set ^= 1;
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<NB>(v2, red, quarter);
             publish_partials<NB>(P, set, v2);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double t2[NB];
             grid_totals_1k<NB>(P, set, t2, quarter);
             set ^= 1;
@@ -991,7 +991,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         const bool want_true = ctl[kCtlTrue] != 0;
         if (tid == 0 && P.true_res && status != CG_ENAN && bb == 0.0) true_rr = 0.0;
         if (want_true) {
-            if (!grid_barrier(P, epoch, S)) goto out;  // every x entry is written
+            if (!grid_barrier<false>(P, epoch, S)) goto out;  // every x entry is written
             double v[1] = {0.0};
             for (int t = t0; t < t1; t += kW) {
                 const double ax = sell_slice_sum<kSellUnrollMem>(M, t, P.x, 0.0);
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             }
             block_sum_1k<1>(v, red, quarter);
             publish_partials<1>(P, set, v);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double tt[1];
             grid_totals_1k<1>(P, set, tt, quarter);
             if (tid == 0) true_rr = tt[0];
@@ -1347,7 +1347,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             v[2] = (double)rz;
             block_sum_1k<3>(v, red, quarter);
             publish_partials<3>(P, set, v);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double tt[3];
             grid_totals_1k<3>(P, set, tt, quarter);
             set ^= 1;
@@ -1397,7 +1397,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             double v1[1] = {(double)pq};
             block_sum_1k<1>(v1, red, quarter);
             publish_partials<1>(P, set, v1);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double sg[1];
             grid_totals_1k<1>(P, set, sg, quarter);
             set ^= 1;
@@ -1431,7 +1431,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
             double v2[2] = {(double)prr, (double)(P.precond ? prz : prr)};
             block_sum_1k<2>(v2, red, quarter);
             publish_partials<2>(P, set, v2);
-            if (!grid_barrier(P, epoch, S)) goto out;
+            if (!grid_barrier<false>(P, epoch, S)) goto out;
             double t2[2];
             grid_totals_1k<2>(P, set, t2, quarter);
             set ^= 1;
@@ -1457,7 +1457,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         for (int t = t0; t < t1; t += kW)
             if (t * 32 + lane < P.n) P.x[t * 32 + lane] += (double)P.d32[t * 32 + lane];
         if (tid == 0) outer = o + 1;
-        if (!grid_barrier(P, epoch, S)) goto out;
+        if (!grid_barrier<false>(P, epoch, S)) goto out;
     }
 
     if (blockIdx.x == 0 && tid == 0) {
