@@ -80,6 +80,13 @@ struct BatchParams {
     double *segpart;             // 2 x nseg x kSlots
     PairState *state;            // ctas x nsys x kRhs
     cg_batch_result *results;    // nsys x kRhs
+    // balanced inner layout (the active tiles split evenly over the CTAs)
+    const int32_t *sys_tile0;    // first tile of each system (nsys + 1)
+    int32_t *bal;                // ctas x 2 (nsys + 1): per CTA, active-tile and active-system prefixes
+    int4 *sinf;                  // ctas x nsys: per CTA, each active system's first and last piece, its
+                                 // segment in the first piece (x, y, z) and whether some piece is empty (w)
+    double *segdyn;              // 2 x ctas x kMaxSegPerCta x kSlots: per-piece segment sums
+    int32_t balance;             // 1: the inner loop may use the balanced layout
 };
 
 __device__ __forceinline__ float f4c(const float4 &v, int r) {
@@ -159,10 +166,9 @@ __device__ __forceinline__ void acc_switch(const BatchParams &B, WarpAcc<T, NS> 
     }
 }
 
-// Zeroes this warp's rows of wpart for the CTA's segments.
-__device__ __forceinline__ void zero_wpart(const BatchParams &B) {
+// Zeroes this warp's rows of wpart for ns segments.
+__device__ __forceinline__ void zero_wpart(const BatchParams &B, int ns) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ns = B.cta_nsys[blockIdx.x];
     double *row = B.wpart + ((size_t)blockIdx.x * kWarps + w) * kMaxSegPerCta * kSlots;
     for (int i = lane; i < ns * kSlots; i += 32) row[i] = 0.0;
     __syncwarp();
@@ -202,42 +208,265 @@ __device__ __forceinline__ auto batch_prefetch(F &f, int i, int) -> decltype(f.p
 template <class F>
 __device__ __forceinline__ void batch_prefetch(F &, int, long) {}
 
-template <class VT, class XT, class AT, class Active, class RowFn, class Acc>
+// ------------------------------------------------------------ tile layouts
+// Which tiles a warp takes in a pass.  The static layout is the plan's split:
+// CTA c owns tiles cta_tile[c] .. cta_tile[c + 1] (balanced over all
+// systems); warp w takes tiles w, w + kWarps, ... of them and skips the tiles
+// of systems the pass's predicate rejects.  As systems converge, that leaves
+// the CTAs holding the slow systems with all the work while the others wait
+// at the barriers.  So the inner loop re-splits whenever a system leaves it:
+// the tiles of the systems still active, in system order, are numbered
+// 0 .. T-1, CTA c takes the piece [floor(c T / G), floor((c + 1) T / G)) and
+// its warp w the tiles w, w + kWarps, ... of the piece.  The segments of a
+// piece are the active systems it touches, in order (at most kMaxSegPerCta,
+// else the static layout is kept).  Every CTA derives the same layout from
+// its copy of the pair states, so a system's partial sums are added in the
+// same order everywhere and results stay bitwise reproducible.
+constexpr int kMaxBalCtas = 320;   // CTAs the layout arrays in shared memory hold
+constexpr int kBalHdr = 2 * kWarps;
+constexpr int kBalArr = kBalHdr + 8;
+static_assert((kBalArr + 3 * kMaxBalCtas) * 4 <= kThreads * 8, "layout arrays fit the block-sum area");
+
+struct Balance {   // the CTA's view of the current layout (shared memory)
+    int dyn;       // 1: balanced layout, 0: the plan's static split
+    int v0, v1;    // this CTA's piece of the active tiles
+    int s0;        // system holding tile v0 (v0 < v1)
+    int k0;        // its active rank
+    int nloc;      // segments of the piece
+    int total;     // T, active tiles
+    int pad;
+};
+
+template <class Active>
+struct StaticTiles {
+    const BatchParams *B;
+    const Active *active;
+    int t, end, s0;
+    __device__ __forceinline__ void skip() {
+        while (t < end && !(*active)(B->tile_sys[t])) t += kWarps;
+    }
+    __device__ __forceinline__ void start(int w) {
+        t = B->P.cta_tile[blockIdx.x] + w;
+        end = B->P.cta_tile[blockIdx.x + 1];
+        s0 = B->cta_sys0[blockIdx.x];
+        skip();
+    }
+    __device__ __forceinline__ bool valid() const { return t < end; }
+    __device__ __forceinline__ int tile() const { return t; }
+    __device__ __forceinline__ int sys() const { return B->tile_sys[t]; }
+    __device__ __forceinline__ int seg() const { return B->tile_sys[t] - s0; }
+    __device__ __forceinline__ void next() {
+        t += kWarps;
+        skip();
+    }
+};
+template <class Active>
+__device__ __forceinline__ StaticTiles<Active> static_tiles(const BatchParams &B, const Active &a) {
+    return StaticTiles<Active>{&B, &a, 0, 0, 0};
+}
+
+// This CTA's prefixes: pfx[s] active tiles and rk[s] active systems before
+// system s (nsys + 1 entries each).
+__device__ __forceinline__ int32_t *bal_pfx(const BatchParams &B) {
+    return B.bal + (size_t)blockIdx.x * 2 * (B.nsys + 1);
+}
+
+// Tiles v0 + w, v0 + w + kWarps, ... < v1 of the active-tile numbering.
+struct BalancedTiles {
+    const BatchParams *B;
+    const int32_t *pfx, *rk;
+    int v, v1, s, k0;
+    __device__ __forceinline__ void settle() {
+        if (v < v1)
+            while (v >= pfx[s + 1]) ++s;
+    }
+    __device__ __forceinline__ void start(int w) {
+        v += w;
+        settle();
+    }
+    __device__ __forceinline__ bool valid() const { return v < v1; }
+    __device__ __forceinline__ int tile() const { return B->sys_tile0[bchk(s, B->nsys)] + (v - pfx[s]); }
+    __device__ __forceinline__ int sys() const { return s; }
+    __device__ __forceinline__ int seg() const { return rk[s] - k0; }
+    __device__ __forceinline__ void next() {
+        v += kWarps;
+        settle();
+    }
+};
+__device__ __forceinline__ BalancedTiles balanced_tiles(const BatchParams &B, const Balance &L) {
+    const int32_t *pfx = bal_pfx(B);
+    return BalancedTiles{&B, pfx, pfx + B.nsys + 1, L.v0, L.v1, L.s0, L.k0};
+}
+
+// The piece holding active tile v: the largest c with floor(c T / G) <= v.
+__device__ __forceinline__ int piece_of(int v, int T, int G) {
+    return (int)(((long long)(v + 1) * G - 1) / T);
+}
+
+// Builds the balanced layout of the systems `active` accepts: this CTA's
+// prefixes and per-system pieces (sinf), every piece's first and last active
+// rank (bsm) and the CTA's own piece (L).  Every CTA checks every piece, so
+// all take the same decision (dyn) and the same layout.  All threads call it;
+// it ends with a __syncthreads.
+template <class Active>
+__device__ void compute_balance(const BatchParams &B, const Active &active, int *bsm) {
+    Balance &L = *reinterpret_cast<Balance *>(bsm + kBalHdr);
+    int *scan = bsm, *k0c = bsm + kBalArr, *k1c = k0c + kMaxBalCtas, *s0c = k1c + kMaxBalCtas;
+    const int ns = B.nsys, G = (int)gridDim.x;
+    int32_t *pfx = bal_pfx(B), *rk = pfx + ns + 1;
+    const int per = (ns + kThreads - 1) / kThreads;
+    const int a = min((int)threadIdx.x * per, ns), b = min(a + per, ns);
+    int tiles = 0, cnt = 0;
+    for (int s = a; s < b; ++s)
+        if (active(s)) {
+            tiles += B.sys_tile0[s + 1] - B.sys_tile0[s];
+            ++cnt;
+        }
+    // exclusive scan of (tiles, cnt) in thread order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int ti = tiles, ci = cnt;
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+        const int tu = __shfl_up_sync(0xffffffffu, ti, m), cu = __shfl_up_sync(0xffffffffu, ci, m);
+        if (lane >= m) {
+            ti += tu;
+            ci += cu;
+        }
+    }
+    if (lane == 31) {
+        scan[w] = ti;
+        scan[kWarps + w] = ci;
+    }
+    for (int c = threadIdx.x; c < G; c += kThreads) k0c[c] = k1c[c] = s0c[c] = 0;
+    __syncthreads();
+    int tb = ti - tiles, cb = ci - cnt, T = 0, K = 0;
+    for (int j = 0; j < kWarps; ++j) {
+        if (j < w) {
+            tb += scan[j];
+            cb += scan[kWarps + j];
+        }
+        T += scan[j];
+        K += scan[kWarps + j];
+    }
+    const long long g = G;
+    for (int s = a; s < b; ++s) {
+        pfx[s] = tb;
+        rk[s] = cb;
+        if (active(s)) {
+            const long long t0 = tb, t1 = tb + (B.sys_tile0[s + 1] - B.sys_tile0[s]);
+            // pieces whose first tile floor(c T / G) lies in [t0, t1)
+            for (long long c = (t0 * g + T - 1) / T; c < g && c * T / g < t1; ++c) {
+                k0c[c] = cb;
+                s0c[c] = s;
+            }
+            // pieces whose last tile floor((c + 1) T / G) - 1 lies in [t0, t1)
+            for (long long c = ((t0 + 1) * g + T - 1) / T - 1; c < g && (c + 1) * T / g <= t1; ++c) k1c[c] = cb;
+            tb = (int)t1;
+            ++cb;
+        }
+    }
+    if (threadIdx.x == 0) {
+        pfx[ns] = T;
+        rk[ns] = K;
+    }
+    __syncthreads();
+    // each system's pieces: c0 .. c1, its segment j0 in piece c0 (0 in the
+    // later ones, which start inside it); with T < G some pieces are empty
+    int4 *sinf = B.sinf + (size_t)blockIdx.x * ns;
+    for (int s = a; s < b; ++s) {
+        const int t0 = pfx[s], t1 = pfx[s + 1];
+        int4 v = make_int4(0, -1, 0, 0);
+        if (t1 > t0) {
+            v.x = piece_of(t0, T, G);
+            v.y = piece_of(t1 - 1, T, G);
+            v.z = rk[s] - k0c[v.x];
+            v.w = T < G;
+        }
+        sinf[s] = v;
+    }
+    int over = 0;
+    for (int c = threadIdx.x; c < G; c += kThreads) {
+        const long long v0 = (long long)c * T / g, v1 = (long long)(c + 1) * T / g;
+        if (v1 > v0 && k1c[c] - k0c[c] + 1 > kMaxSegPerCta) over = 1;
+    }
+    over = __syncthreads_or(over);
+    if (threadIdx.x == 0) {
+        const int c = blockIdx.x;
+        const int v0 = T > 0 ? (int)((long long)c * T / g) : 0, v1 = T > 0 ? (int)((long long)(c + 1) * T / g) : 0;
+        const bool mine = v1 > v0;
+        L.dyn = (T > 0 && !over) ? 1 : 0;
+        L.total = T;
+        L.v0 = v0;
+        L.v1 = v1;
+        L.s0 = mine ? s0c[c] : 0;
+        L.k0 = mine ? k0c[c] : 0;
+        L.nloc = mine ? k1c[c] - k0c[c] + 1 : 0;
+    }
+    __syncthreads();
+}
+
+// Adds the 16 warp rows of each of this piece's nloc segments (fixed order)
+// into segdyn[set][c], for the first nslots slots.
+__device__ __forceinline__ void combine_segments_dyn(const BatchParams &B, int set, int nslots, int nloc) {
+    __syncthreads();
+    const double *wp = B.wpart + (size_t)blockIdx.x * kWarps * kMaxSegPerCta * kSlots;
+    double *dst = B.segdyn + ((size_t)set * gridDim.x + blockIdx.x) * kMaxSegPerCta * kSlots;
+    for (int q = threadIdx.x; q < nloc * nslots; q += kThreads) {
+        const int j = q / nslots, i = q % nslots;
+        double s = 0.0;
+        for (int w = 0; w < kWarps; ++w) s += wp[((size_t)w * kMaxSegPerCta + j) * kSlots + i];
+        dst[(size_t)j * kSlots + i] = s;
+    }
+}
+
+// Totals of slots sl[0..NS) for one system under the balanced layout: the
+// system's segments in the pieces it spans, in piece order (zero for a
+// system outside the layout).
+template <int NS>
+__device__ __forceinline__ void system_totals_dyn(const BatchParams &B, int set, int total, int sys,
+                                                  const int (&sl)[NS], float (&out)[NS]) {
+    const int4 v = B.sinf[(size_t)blockIdx.x * B.nsys + sys];
+    const int G = (int)gridDim.x;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) out[i] = 0.0f;
+    for (int c = v.x; c <= v.y; ++c) {
+        // an empty piece (fewer active tiles than CTAs) holds nothing
+        if (v.w && c * total / G == (c + 1) * total / G) continue;
+        const int j = c == v.x ? bchk(v.z, kMaxSegPerCta) : 0;
+        const double *src = B.segdyn + (((size_t)set * G + c) * kMaxSegPerCta + j) * kSlots;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) out[i] += (float)__ldcg(src + sl[i]);
+    }
+}
+
+template <class VT, class XT, class AT, class Cur, class RowFn, class Acc>
 __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, uint32_t &count,
-                                           const VT *vals, const XT *x, const Active &active, RowFn &rowfn,
+                                           const VT *vals, const XT *x, Cur cur, RowFn &rowfn,
                                            Acc &acc) {
     const Params &P = B.P;
-    const int t0 = P.cta_tile[blockIdx.x], nt = P.cta_tile[blockIdx.x + 1] - t0;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s0 = B.cta_sys0[blockIdx.x];
     bool ok = true;
+    cur.start(w);
     if (vals == nullptr) {
-        for (int t = t0 + w; t < t0 + nt; t += kWarps) {
-            const int sys = B.tile_sys[t];
-            if (!active(sys)) continue;
-            acc_switch(B, acc, sys - s0);
-            const TileDesc d = load_desc(P, t);
+        for (; cur.valid(); cur.next()) {
+            const int sys = cur.sys();
+            acc_switch(B, acc, cur.seg());
+            const TileDesc d = load_desc(P, cur.tile());
             const int row = d.r0 + lane;
             if (row < d.r1) rowfn(sys, row, AT{}, acc);
         }
     } else {
-        // next active tile at or after t
-        auto next_active = [&](int t) {
-            while (t < t0 + nt && !active(B.tile_sys[t])) t += kWarps;
-            return t;
-        };
-        int cur = next_active(t0 + w);
-        if (cur < t0 + nt) {
-            const TileDesc d = load_desc(P, cur);
+        if (cur.valid()) {
+            const TileDesc d = load_desc(P, cur.tile());
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) issue_matrix<VT, XT>(P, S, d, w, vals);
             __syncwarp();
             issue_window<VT, XT>(P, S, d, w, x);
         }
-        while (cur < t0 + nt) {
-            const TileDesc d = load_desc(P, cur);
-            const int sys = B.tile_sys[cur];
+        while (cur.valid()) {
+            const TileDesc d = load_desc(P, cur.tile());
+            const int sys = cur.sys();
             store_tail<VT, XT>(P, S, d, w, x);
             if (B.lanes_per_row == 1 && d.kind != kTileLong && d.r0 + lane < d.r1) batch_prefetch(rowfn, d.r0 + lane, 0);
             const bool got = mbar_wait_bounded(&S.mbar[w], count & 1u, P.wait_ns);
@@ -246,7 +475,7 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
                 break;
             }
             __syncwarp();
-            acc_switch(B, acc, sys - s0);
+            acc_switch(B, acc, cur.seg());
             const int row = d.r0 + lane;
             if (d.kind == kTileLong) {
                 AT part{};
@@ -283,16 +512,17 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
             }
             __syncwarp();
             ++count;
-            const int nxt = next_active(cur + kWarps);
-            if (nxt < t0 + nt) {
-                const TileDesc dn = load_desc(P, nxt);
+            Cur nx = cur;
+            nx.next();
+            if (nx.valid()) {
+                const TileDesc dn = load_desc(P, nx.tile());
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) issue_matrix<VT, XT>(P, S, dn, w, vals);
                 __syncwarp();
                 issue_window<VT, XT>(P, S, dn, w, x);
             }
-            cur = nxt;
+            cur = nx;
         }
     }
     if (acc.seg >= 0) flush_acc(B, acc);
@@ -343,6 +573,9 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Smem S = carve_smem(smem_raw);
     init_pipeline(S);
+    // the block-sum area is free in this kernel: it holds the layout arrays
+    int *const bsm = reinterpret_cast<int *>(S.red);
+    Balance &bl = *reinterpret_cast<Balance *>(bsm + kBalHdr);
     const Params &P = B.P;
     unsigned int epoch = 0;
     uint32_t count = 0;
@@ -370,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
 
     for (int o = 0;; ++o) {
         // ------------------------------------------ outer residual (FP64)
-        zero_wpart(B);
+        zero_wpart(B, B.cta_nsys[blockIdx.x]);
         for (int r = 0; r < nrhs; ++r) {
             WarpAcc<double, 12> acc;
             acc.seg = -1;
@@ -399,8 +632,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                 B.d32[i] = v;
                 a.a[8 + r] = fma((double)rf, (double)zf, a.a[8 + r]);
             };
-            if (!batch_pass<double, double, double>(B, S, count, P.vals, B.xw + (size_t)r * B.xstride, active,
-                                                    rowfn, acc))
+            if (!batch_pass<double, double, double>(B, S, count, P.vals, B.xw + (size_t)r * B.xstride,
+                                                    static_tiles(B, active), rowfn, acc))
                 goto out;
         }
         combine_segments(B, set, 12);
@@ -448,46 +681,72 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
             set ^= 1;
             if (__syncthreads_or(inner_any)) {
                 // ------------------------------------------ inner CG (FP32, 4 rhs)
+                auto active = [&](int sys) { return any_flag(sys, kInnerActive); };
+                if (B.balance) compute_balance(B, active, bsm);
+                else if (threadIdx.x == 0) bl.dyn = 0;
+                __syncthreads();
                 for (int k = 1;; ++k) {
-                    auto active = [&](int sys) { return any_flag(sys, kInnerActive); };
+                    const bool dyn = bl.dyn != 0;
+                    const int nloc = dyn ? bl.nloc : B.cta_nsys[blockIdx.x];
                     // p = z + beta p, q = A_lo z + beta q (= A_lo p); p.q
                     // (the SpMM gathers z: A p = A z + beta A p_old)
-                    zero_wpart(B);
+                    zero_wpart(B, nloc);
                     {
                         WarpAcc<float, 4> acc;
                         acc.seg = -1;
                         SpmmRow rowfn{B, st};
-                        if (!batch_pass<VT, float4, float4>(B, S, count, vlo, B.p32, active, rowfn, acc)) goto out;
+                        const bool ok =
+                            dyn ? batch_pass<VT, float4, float4>(B, S, count, vlo, B.p32, balanced_tiles(B, bl), rowfn, acc)
+                                : batch_pass<VT, float4, float4>(B, S, count, vlo, B.p32, static_tiles(B, active), rowfn,
+                                                                 acc);
+                        if (!ok) goto out;
                     }
-                    combine_segments(B, set, 4);
+                    if (dyn) combine_segments_dyn(B, set, 4, nloc);
+                    else combine_segments(B, set, 4);
                     if (!grid_barrier(P, epoch, S)) goto out;
+                    int left_now = 0;
                     for (int q = threadIdx.x; q < npairs; q += kThreads) {
                         PairState ps = st[q];
                         ps.alpha = 0.0f;
                         if (ps.flags & kInnerActive) {
-                            const float sg = system_total<float>(B, set, q / kRhs, q % kRhs);
-                            if (!(sg > 0.0f) || !isfinite(sg)) ps.flags &= ~kInnerActive;  // keep d so far
-                            else ps.alpha = (float)ps.rho / sg;
+                            float sg;
+                            if (dyn) {
+                                const int sl[1] = {q % kRhs};
+                                float o[1];
+                                system_totals_dyn<1>(B, set, bl.total, q / kRhs, sl, o);
+                                sg = o[0];
+                            } else {
+                                sg = system_total<float>(B, set, q / kRhs, q % kRhs);
+                            }
+                            if (!(sg > 0.0f) || !isfinite(sg)) {
+                                ps.flags &= ~kInnerActive;  // keep d so far
+                                left_now = 1;
+                            } else {
+                                ps.alpha = (float)ps.rho / sg;
+                            }
                         }
                         st[q] = ps;
                     }
                     __syncthreads();
                     set ^= 1;
                     // d += alpha p, r -= alpha q, z = dinv r (gathered by the next SpMM:
-                    // every gather of this one is over); r.r, r.z
-                    zero_wpart(B);
+                    // every gather of this one is over); r.r, r.z.  A pair that is not
+                    // in the inner loop (any more) keeps its d and r.
+                    zero_wpart(B, nloc);
                     {
                         WarpAcc<float, 8> acc;
                         acc.seg = -1;
                         auto rowfn = [&](int sys, int i, float4, WarpAcc<float, 8> &a) {
                             const PairState *pp = st + sys * kRhs;
+                            const bool u0 = (pp[0].flags & kInnerActive) != 0, u1 = (pp[1].flags & kInnerActive) != 0,
+                                       u2 = (pp[2].flags & kInnerActive) != 0, u3 = (pp[3].flags & kInnerActive) != 0;
                             const float al0 = pp[0].alpha, al1 = pp[1].alpha, al2 = pp[2].alpha, al3 = pp[3].alpha;
                             const float4 p = B.pd32[i], qv = B.q32[i];
                             float4 d = B.d32[i], rv = B.r32[i];
-                            d = make_float4(fmaf(al0, p.x, d.x), fmaf(al1, p.y, d.y), fmaf(al2, p.z, d.z),
-                                            fmaf(al3, p.w, d.w));
-                            rv = make_float4(fmaf(-al0, qv.x, rv.x), fmaf(-al1, qv.y, rv.y), fmaf(-al2, qv.z, rv.z),
-                                             fmaf(-al3, qv.w, rv.w));
+                            d = make_float4(u0 ? fmaf(al0, p.x, d.x) : d.x, u1 ? fmaf(al1, p.y, d.y) : d.y,
+                                            u2 ? fmaf(al2, p.z, d.z) : d.z, u3 ? fmaf(al3, p.w, d.w) : d.w);
+                            rv = make_float4(u0 ? fmaf(-al0, qv.x, rv.x) : rv.x, u1 ? fmaf(-al1, qv.y, rv.y) : rv.y,
+                                             u2 ? fmaf(-al2, qv.z, rv.z) : rv.z, u3 ? fmaf(-al3, qv.w, rv.w) : rv.w);
                             B.d32[i] = d;
                             B.r32[i] = rv;
                             float4 z = rv;
@@ -505,24 +764,40 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                             a.a[6] = fmaf(rv.z, z.z, a.a[6]);
                             a.a[7] = fmaf(rv.w, z.w, a.a[7]);
                         };
-                        if (!batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr, (const float4 *)nullptr,
-                                                            active, rowfn, acc))
-                            goto out;
+                        const bool ok =
+                            dyn ? batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr,
+                                                                 (const float4 *)nullptr, balanced_tiles(B, bl), rowfn,
+                                                                 acc)
+                                : batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr,
+                                                                 (const float4 *)nullptr, static_tiles(B, active), rowfn,
+                                                                 acc);
+                        if (!ok) goto out;
                     }
-                    combine_segments(B, set, 8);
+                    if (dyn) combine_segments_dyn(B, set, 8, nloc);
+                    else combine_segments(B, set, 8);
                     if (!grid_barrier(P, epoch, S)) goto out;
                     int left = 0;
                     for (int q = threadIdx.x; q < npairs; q += kThreads) {
                         PairState ps = st[q];
                         ps.beta = 0.0f;
                         if (ps.flags & kInnerActive) {
-                            const int sys = q / kRhs, r = q % kRhs;
-                            const float rr = system_total<float>(B, set, sys, r);
-                            const float rz = system_total<float>(B, set, sys, 4 + r);
+                            const int r = q % kRhs;
+                            float rr, rz;
+                            if (dyn) {
+                                const int sl[2] = {r, 4 + r};
+                                float o[2];
+                                system_totals_dyn<2>(B, set, bl.total, q / kRhs, sl, o);
+                                rr = o[0];
+                                rz = o[1];
+                            } else {
+                                rr = system_total<float>(B, set, q / kRhs, r);
+                                rz = system_total<float>(B, set, q / kRhs, 4 + r);
+                            }
                             ++ps.iters;
                             if (!isfinite(rr) || !isfinite(rz) || !(rz > 0.0f) || (double)rr <= ps.target2 ||
                                 k >= B.max_inner || ps.iters >= B.maxit) {
                                 ps.flags &= ~kInnerActive;
+                                left_now = 1;
                             } else {
                                 ps.beta = rz / (float)ps.rho;
                                 ps.rho = rz;
@@ -533,6 +808,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     }
                     set ^= 1;
                     if (!__syncthreads_or(left)) break;
+                    // a pair left the inner loop: its system may have, so re-split
+                    if (B.balance && __syncthreads_or(left_now)) compute_balance(B, active, bsm);
                 }
             }
         }
@@ -557,7 +834,8 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                         x = ps.rho < 0.0 ? 0.0 : x + (double)f4c(d, r);
                     }
                 };
-                if (!batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr, (const float4 *)nullptr, active,
+                if (!batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr, (const float4 *)nullptr,
+                                                    static_tiles(B, active),
                                                     rowfn, acc))
                     goto out;
             }
@@ -600,6 +878,9 @@ struct cg_batch {
     // device
     int32_t *rowptr = nullptr, *colidx = nullptr, *tile_sys = nullptr, *cta_tile = nullptr;
     int32_t *cta_sys0 = nullptr, *cta_nsys = nullptr, *cta_seg0 = nullptr, *sys_seg0 = nullptr;
+    int32_t *sys_tile0 = nullptr, *bal = nullptr;
+    int4 *sinf = nullptr;
+    double *segdyn = nullptr;
     int4 *tiles_win = nullptr, *tiles_gather = nullptr, *segs = nullptr;
     uint16_t *lcol = nullptr, *vals16 = nullptr;
     double *vals = nullptr, *xw = nullptr, *wpart = nullptr, *segpart = nullptr;
@@ -701,6 +982,11 @@ BatchParams batch_params(const cg_batch *h, const double *Bm, int nrhs, double t
     B.segpart = h->segpart;
     B.state = h->state;
     B.results = h->results;
+    B.sys_tile0 = h->sys_tile0;
+    B.bal = h->bal;
+    B.sinf = h->sinf;
+    B.segdyn = h->segdyn;
+    B.balance = h->ctas <= kMaxBalCtas ? 1 : 0;
     return B;
 }
 
@@ -857,6 +1143,10 @@ int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in,
         I4 &d1 = desc_gather[2 * t + 1];
         if (d1.w == kTileWindow) d1 = mk4(0, 0, 0, kTileGather);
     }
+    // first tile of each system (tiles are in system order)
+    std::vector<int32_t> sys_tile0((size_t)nsys + 1, 0);
+    for (int32_t s : bp.tile_sys) ++sys_tile0[(size_t)s + 1];
+    for (int s = 0; s < nsys; ++s) sys_tile0[(size_t)s + 1] += sys_tile0[s];
     h->ctas = ctas;
     h->nseg = (int)bp.seg_cta.size();
     h->ntiles = (int)bp.tile_sys.size();
@@ -873,6 +1163,10 @@ int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in,
         (rc = bdev_alloc(h, &h->cta_nsys, bp.cta_nsys.size())) ||
         (rc = bdev_alloc(h, &h->cta_seg0, bp.cta_seg0.size())) ||
         (rc = bdev_alloc(h, &h->sys_seg0, bp.sys_seg0.size())) || (rc = bdev_alloc(h, &h->diag_lo, (size_t)n + 1)) ||
+        (rc = bdev_alloc(h, &h->sys_tile0, sys_tile0.size())) ||
+        (rc = bdev_alloc(h, &h->bal, (size_t)ctas * 2 * ((size_t)nsys + 1))) ||
+        (rc = bdev_alloc(h, &h->sinf, (size_t)ctas * nsys)) ||
+        (rc = bdev_alloc(h, &h->segdyn, (size_t)2 * ctas * kMaxSegPerCta * kSlots)) ||
         (rc = bdev_alloc(h, &h->xw, (size_t)kRhs * h->xstride)) ||
         (rc = bdev_alloc(h, &h->r32, (size_t)n + 1)) || (rc = bdev_alloc(h, &h->p32, (size_t)n + pad)) ||
         (rc = bdev_alloc(h, &h->pd32, (size_t)n + 1)) ||
@@ -913,6 +1207,7 @@ int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts_in,
         (rc = bupload(h->tile_sys, bp.tile_sys)) || (rc = bupload(h->cta_tile, bp.cut)) ||
         (rc = bupload(h->cta_sys0, bp.cta_sys0)) || (rc = bupload(h->cta_nsys, bp.cta_nsys)) ||
         (rc = bupload(h->cta_seg0, bp.cta_seg0)) || (rc = bupload(h->sys_seg0, bp.sys_seg0)) ||
+        (rc = bupload(h->sys_tile0, sys_tile0)) ||
         (rc = bupload(h->diag_lo, inner.diag)))
         return fail(rc);
     if (opts.inner_values == CG_VALUES_FP32) {
