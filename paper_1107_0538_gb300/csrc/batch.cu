@@ -448,16 +448,33 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
     bool ok = true;
     cur.start(w);
     if (vals == nullptr) {
-        for (; cur.valid(); cur.next()) {
-            const int sys = cur.sys();
+        // the next tile's descriptor and row loads (prefetch) are issued
+        // before the current tile's rows are finished: two tiles in flight
+        TileDesc d{};
+        if (cur.valid()) {
+            d = load_desc(P, cur.tile());
+            if (d.r0 + lane < d.r1) batch_prefetch(rowfn, d.r0 + lane, 0);
+        }
+        while (cur.valid()) {
+            Cur nx = cur;
+            nx.next();
+            TileDesc dn{};
+            if (nx.valid()) {
+                dn = load_desc(P, nx.tile());
+                if (dn.r0 + lane < dn.r1) batch_prefetch(rowfn, dn.r0 + lane, 0);
+            }
             acc_switch(B, acc, cur.seg());
-            const TileDesc d = load_desc(P, cur.tile());
             const int row = d.r0 + lane;
-            if (row < d.r1) rowfn(sys, row, AT{}, acc);
+            if (row < d.r1) rowfn(cur.sys(), row, AT{}, acc);
+            d = dn;
+            cur = nx;
         }
     } else {
+        // the descriptor loaded to issue a tile's copies is kept for its turn
+        TileDesc dc{};
         if (cur.valid()) {
             const TileDesc d = load_desc(P, cur.tile());
+            dc = d;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) issue_matrix<VT, XT>(P, S, d, w, vals);
@@ -465,7 +482,7 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
             issue_window<VT, XT>(P, S, d, w, x);
         }
         while (cur.valid()) {
-            const TileDesc d = load_desc(P, cur.tile());
+            const TileDesc d = dc;
             const int sys = cur.sys();
             store_tail<VT, XT>(P, S, d, w, x);
             if (B.lanes_per_row == 1 && d.kind != kTileLong && d.r0 + lane < d.r1) batch_prefetch(rowfn, d.r0 + lane, 0);
@@ -516,6 +533,7 @@ __device__ __forceinline__ bool batch_pass(const BatchParams &B, const Smem &S, 
             nx.next();
             if (nx.valid()) {
                 const TileDesc dn = load_desc(P, nx.tile());
+                dc = dn;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) issue_matrix<VT, XT>(P, S, dn, w, vals);
@@ -564,6 +582,72 @@ struct SpmmRow {
         a.a[1] = fmaf(p.y, qv.y, a.a[1]);
         a.a[2] = fmaf(p.z, qv.z, a.a[2]);
         a.a[3] = fmaf(p.w, qv.w, a.a[3]);
+    }
+};
+
+// Row function of the inner update pass: d += alpha p, r -= alpha q, z =
+// dinv r (published: the SpMM of the next iteration gathers it), r.r and r.z
+// per right-hand side.  A pair that is not in the inner loop (any more) keeps
+// its d and r.  prefetch(i) loads row i's vectors ahead into one of two
+// slots: the pass issues the next tile's loads before it finishes the
+// current one, so each lane has two rows' loads in flight.
+struct UpdateRow {
+    const BatchParams &B;
+    const PairState *st;
+    int i0 = -1, i1 = -1, nxt = 0;
+    float4 p0, q0, d0, r0, p1, q1, d1, r1;
+    float di0 = 1.0f, di1 = 1.0f;
+    __device__ __forceinline__ void prefetch(int i) {
+        const float4 p = B.pd32[i], q = B.q32[i], d = B.d32[i], r = B.r32[i];
+        const float di = B.P.precond ? B.P.dinv32[i] : 1.0f;
+        if (nxt == 0) {
+            i0 = i;
+            p0 = p;
+            q0 = q;
+            d0 = d;
+            r0 = r;
+            di0 = di;
+        } else {
+            i1 = i;
+            p1 = p;
+            q1 = q;
+            d1 = d;
+            r1 = r;
+            di1 = di;
+        }
+        nxt ^= 1;
+    }
+    __device__ __forceinline__ void operator()(int sys, int i, float4, WarpAcc<float, 8> &a) {
+        const PairState *pp = st + sys * kRhs;
+        const bool u0 = (pp[0].flags & kInnerActive) != 0, u1 = (pp[1].flags & kInnerActive) != 0,
+                   u2 = (pp[2].flags & kInnerActive) != 0, u3 = (pp[3].flags & kInnerActive) != 0;
+        const float al0 = pp[0].alpha, al1 = pp[1].alpha, al2 = pp[2].alpha, al3 = pp[3].alpha;
+        float4 p, qv, d, rv;
+        float di;
+        if (i == i0) {
+            p = p0, qv = q0, d = d0, rv = r0, di = di0;
+        } else if (i == i1) {
+            p = p1, qv = q1, d = d1, rv = r1, di = di1;
+        } else {
+            p = B.pd32[i], qv = B.q32[i], d = B.d32[i], rv = B.r32[i];
+            di = B.P.precond ? B.P.dinv32[i] : 1.0f;
+        }
+        d = make_float4(u0 ? fmaf(al0, p.x, d.x) : d.x, u1 ? fmaf(al1, p.y, d.y) : d.y,
+                        u2 ? fmaf(al2, p.z, d.z) : d.z, u3 ? fmaf(al3, p.w, d.w) : d.w);
+        rv = make_float4(u0 ? fmaf(-al0, qv.x, rv.x) : rv.x, u1 ? fmaf(-al1, qv.y, rv.y) : rv.y,
+                         u2 ? fmaf(-al2, qv.z, rv.z) : rv.z, u3 ? fmaf(-al3, qv.w, rv.w) : rv.w);
+        B.d32[i] = d;
+        B.r32[i] = rv;
+        const float4 z = B.P.precond ? make_float4(di * rv.x, di * rv.y, di * rv.z, di * rv.w) : rv;
+        B.p32[i] = z;
+        a.a[0] = fmaf(rv.x, rv.x, a.a[0]);
+        a.a[1] = fmaf(rv.y, rv.y, a.a[1]);
+        a.a[2] = fmaf(rv.z, rv.z, a.a[2]);
+        a.a[3] = fmaf(rv.w, rv.w, a.a[3]);
+        a.a[4] = fmaf(rv.x, z.x, a.a[4]);
+        a.a[5] = fmaf(rv.y, z.y, a.a[5]);
+        a.a[6] = fmaf(rv.z, z.z, a.a[6]);
+        a.a[7] = fmaf(rv.w, z.w, a.a[7]);
     }
 };
 
@@ -730,40 +814,12 @@ __global__ void __launch_bounds__(kThreads, 1) cg_batch_kernel(BatchParams B) {
                     __syncthreads();
                     set ^= 1;
                     // d += alpha p, r -= alpha q, z = dinv r (gathered by the next SpMM:
-                    // every gather of this one is over); r.r, r.z.  A pair that is not
-                    // in the inner loop (any more) keeps its d and r.
+                    // every gather of this one is over); r.r, r.z
                     zero_wpart(B, nloc);
                     {
                         WarpAcc<float, 8> acc;
                         acc.seg = -1;
-                        auto rowfn = [&](int sys, int i, float4, WarpAcc<float, 8> &a) {
-                            const PairState *pp = st + sys * kRhs;
-                            const bool u0 = (pp[0].flags & kInnerActive) != 0, u1 = (pp[1].flags & kInnerActive) != 0,
-                                       u2 = (pp[2].flags & kInnerActive) != 0, u3 = (pp[3].flags & kInnerActive) != 0;
-                            const float al0 = pp[0].alpha, al1 = pp[1].alpha, al2 = pp[2].alpha, al3 = pp[3].alpha;
-                            const float4 p = B.pd32[i], qv = B.q32[i];
-                            float4 d = B.d32[i], rv = B.r32[i];
-                            d = make_float4(u0 ? fmaf(al0, p.x, d.x) : d.x, u1 ? fmaf(al1, p.y, d.y) : d.y,
-                                            u2 ? fmaf(al2, p.z, d.z) : d.z, u3 ? fmaf(al3, p.w, d.w) : d.w);
-                            rv = make_float4(u0 ? fmaf(-al0, qv.x, rv.x) : rv.x, u1 ? fmaf(-al1, qv.y, rv.y) : rv.y,
-                                             u2 ? fmaf(-al2, qv.z, rv.z) : rv.z, u3 ? fmaf(-al3, qv.w, rv.w) : rv.w);
-                            B.d32[i] = d;
-                            B.r32[i] = rv;
-                            float4 z = rv;
-                            if (P.precond) {
-                                const float di = P.dinv32[i];
-                                z = make_float4(di * rv.x, di * rv.y, di * rv.z, di * rv.w);
-                            }
-                            B.p32[i] = z;
-                            a.a[0] = fmaf(rv.x, rv.x, a.a[0]);
-                            a.a[1] = fmaf(rv.y, rv.y, a.a[1]);
-                            a.a[2] = fmaf(rv.z, rv.z, a.a[2]);
-                            a.a[3] = fmaf(rv.w, rv.w, a.a[3]);
-                            a.a[4] = fmaf(rv.x, z.x, a.a[4]);
-                            a.a[5] = fmaf(rv.y, z.y, a.a[5]);
-                            a.a[6] = fmaf(rv.z, z.z, a.a[6]);
-                            a.a[7] = fmaf(rv.w, z.w, a.a[7]);
-                        };
+                        UpdateRow rowfn{B, st};
                         const bool ok =
                             dyn ? batch_pass<VT, float4, float4>(B, S, count, (const VT *)nullptr,
                                                                  (const float4 *)nullptr, balanced_tiles(B, bl), rowfn,
