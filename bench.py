@@ -314,6 +314,16 @@ def measure_batched(nsys: int, emin: int, emax: int, steps: int, tune_sys: int, 
                 "ms_per_solve_amortised": round(batch_ms / len(res), 4),
                 "inner_iters_max": max(r.iters for r in res), "outer_max": max(r.outer for r in res),
                 "relres_max": max(r.relres for r in res)})
+    # the same solve with the inner loop keeping the creation-time split of
+    # the tiles instead of re-splitting the active ones over the CTAs
+    if choice is not None:
+        bs.set_tuning(*choice, 1)
+        X.zero_()
+        torch.cuda.synchronize()
+        rcs, ress, ms_static = bs.solve(B, X, TOL)
+        out["static_split"] = {"ms_per_batch": round(ms_static, 3), "status": rcs,
+                               "pairs_converged": sum(1 for r in ress if r.status == gbcg.CG_OK)}
+        bs.set_tuning(*choice, 0)
     # the whole batch's enqueue (copies, memsets, the cooperative launch)
     # captured in one CUDA graph and replayed
     try:

@@ -279,7 +279,12 @@ typedef struct {
     int32_t lanes_per_row;   /* lanes that share one row in the inner SpMM: 1, 2
                                 or 4 (a warp steps through a 32-row tile 32, 16
                                 or 8 rows at a time)                              */
-    int32_t reserved;        /* 0                                                 */
+    int32_t static_split;    /* 0: the inner loop re-splits the tiles of the
+                                systems still active evenly over the CTAs each
+                                time a system leaves it; 1: it keeps the
+                                creation-time split over all systems (not
+                                searched by cg_batch_tune, which reports the
+                                handle's setting)                                 */
 } cg_batch_tuning;
 
 typedef struct cg_batch cg_batch;
@@ -293,7 +298,9 @@ typedef struct cg_batch cg_batch;
  * right-hand side) pair runs the mixed-precision refinement of cg_solve
  * (opts->inner_values FP32 or BF16; FP64 is taken as FP32; precond applies
  * to the inner CG) and all pairs advance in lockstep inside one persistent
- * cooperative kernel; tiles of finished systems are skipped.  A CTA may
+ * cooperative kernel; tiles of finished systems are skipped, and the inner
+ * loop re-splits the tiles still active evenly over the CTAs (deterministic:
+ * results are bitwise reproducible).  A CTA may
  * hold tiles of at most 64 systems (CG_EINVAL otherwise).  Synchronous.
  */
 int cg_batch_create(const cg_csr *systems, int32_t nsys, const cg_opts *opts, void *stream,
@@ -339,8 +346,8 @@ int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double 
 /*
  * Applies a choice (for example one cg_batch_tune found on a smaller batch
  * of the same kind of systems): inner_tol in (0, 1), gather_tiles 0 or 1,
- * lanes_per_row 1, 2 or 4; trials and best_ms are ignored.  CG_EINVAL
- * otherwise.  Takes effect at the next enqueue.
+ * lanes_per_row 1, 2 or 4, static_split 0 or 1; trials and best_ms are
+ * ignored.  CG_EINVAL otherwise.  Takes effect at the next enqueue.
  */
 int cg_batch_set_tuning(cg_batch *h, const cg_batch_tuning *choice);
 

@@ -930,6 +930,7 @@ struct cg_batch {
     double inner_tol = 1e-3;
     int use_gather = 0;                 // tuned: 1 = gather tiles instead of x-windows
     int lanes_per_row = 1;              // tuned: SpMM lanes per row (rows per warp step 32 / this)
+    int static_split = 0;               // 1: the inner loop keeps the creation-time split
     std::vector<int32_t> sys_rows;
     // device
     int32_t *rowptr = nullptr, *colidx = nullptr, *tile_sys = nullptr, *cta_tile = nullptr;
@@ -1042,7 +1043,7 @@ BatchParams batch_params(const cg_batch *h, const double *Bm, int nrhs, double t
     B.bal = h->bal;
     B.sinf = h->sinf;
     B.segdyn = h->segdyn;
-    B.balance = h->ctas <= kMaxBalCtas ? 1 : 0;
+    B.balance = (h->ctas <= kMaxBalCtas && !h->static_split) ? 1 : 0;
     return B;
 }
 
@@ -1366,7 +1367,7 @@ int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double 
         choice->trials = tried;
         choice->best_ms = best_ms < 1e300 ? best_ms : -1.0;
         choice->lanes_per_row = best_lanes;
-        choice->reserved = 0;
+        choice->static_split = h->static_split;
     }
     if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
     return rc;
@@ -1375,11 +1376,13 @@ int cg_batch_tune(cg_batch *h, const double *B, double *X, int32_t nrhs, double 
 int cg_batch_set_tuning(cg_batch *h, const cg_batch_tuning *choice) {
     if (!h || !choice) return CG_EINVAL;
     if (!(choice->inner_tol > 0.0 && choice->inner_tol < 1.0) || (choice->gather_tiles != 0 && choice->gather_tiles != 1) ||
-        (choice->lanes_per_row != 1 && choice->lanes_per_row != 2 && choice->lanes_per_row != 4))
+        (choice->lanes_per_row != 1 && choice->lanes_per_row != 2 && choice->lanes_per_row != 4) ||
+        (choice->static_split != 0 && choice->static_split != 1))
         return CG_EINVAL;
     h->inner_tol = choice->inner_tol;
     h->use_gather = choice->gather_tiles;
     h->lanes_per_row = choice->lanes_per_row;
+    h->static_split = choice->static_split;
     return CG_OK;
 }
 

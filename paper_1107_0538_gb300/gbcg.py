@@ -89,7 +89,7 @@ class cg_batch_result(ctypes.Structure):
 class cg_batch_tuning(ctypes.Structure):
     _fields_ = [("inner_tol", ctypes.c_double), ("gather_tiles", ctypes.c_int32),
                 ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double),
-                ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lanes_per_row", ctypes.c_int32), ("static_split", ctypes.c_int32)]
 
 
 class cg_learn_set(ctypes.Structure):
@@ -446,8 +446,9 @@ class BatchSolver:
     def tune(self, B, X, tol: float):
         return cg_batch_tune(self.h, B.data_ptr(), X.data_ptr(), B.shape[0], tol)
 
-    def set_tuning(self, inner_tol: float, gather_tiles: int, lanes_per_row: int) -> None:
-        c = cg_batch_tuning(inner_tol=inner_tol, gather_tiles=gather_tiles, lanes_per_row=lanes_per_row)
+    def set_tuning(self, inner_tol: float, gather_tiles: int, lanes_per_row: int, static_split: int = 0) -> None:
+        c = cg_batch_tuning(inner_tol=inner_tol, gather_tiles=gather_tiles, lanes_per_row=lanes_per_row,
+                            static_split=static_split)
         rc = cg_batch_set_tuning(self.h, c)
         if rc != CG_OK:
             raise GbcgError(rc, "cg_batch_set_tuning")

@@ -65,7 +65,7 @@ int main(void) {
   F(cg_batch_result, iters) F(cg_batch_result, outer) F(cg_batch_result, status) F(cg_batch_result, reserved)
   F(cg_batch_result, relres)
   F(cg_batch_tuning, inner_tol) F(cg_batch_tuning, gather_tiles) F(cg_batch_tuning, trials) F(cg_batch_tuning, best_ms)
-  F(cg_batch_tuning, lanes_per_row) F(cg_batch_tuning, reserved)
+  F(cg_batch_tuning, lanes_per_row) F(cg_batch_tuning, static_split)
   F(cg_learn_set, ninst) F(cg_learn_set, inst) F(cg_learn_set, npairs) F(cg_learn_set, pair_inst)
   F(cg_learn_set, r) F(cg_learn_set, e)
   printf("\\"sizes\\": [%zu, %zu, %zu, %zu]}", sizeof(cg_csr), sizeof(cg_opts), sizeof(cg_info), sizeof(cg_plan));

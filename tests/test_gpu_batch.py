@@ -161,15 +161,17 @@ def test_batch_graph_capture_replay_matches_oracle(dev):
         del g
 
 
+@pytest.mark.parametrize("split", [0, 1], ids=["resplit", "static"])
 @pytest.mark.parametrize("lanes", [1, 2, 4])
 @pytest.mark.parametrize("gather", [0, 1], ids=["window", "gather"])
-def test_batch_tuning_choices_match_oracle(dev, lanes, gather):
+def test_batch_tuning_choices_match_oracle(dev, lanes, gather, split):
     """Every point the tuner can choose (tile kind x lanes per row of the
-    inner SpMM), applied with cg_batch_set_tuning, gives pairs that pass the
-    oracle checks; invalid choices are refused."""
+    inner SpMM), with the inner loop re-splitting the active tiles or keeping
+    the creation-time split, applied with cg_batch_set_tuning, gives pairs
+    that pass the oracle checks; invalid choices are refused."""
     sl = systems(5)
     with gbcg.BatchSolver([s["A"] for s in sl], precond=1) as bs:
-        bs.set_tuning(3e-3, gather, lanes)
+        bs.set_tuning(3e-3, gather, lanes, split)
         B = torch.from_numpy(stacked(sl, 4)).to(dev).contiguous()
         X = torch.zeros_like(B)
         rc, res, ms = bs.solve(B, X, TOL)
@@ -177,5 +179,6 @@ def test_batch_tuning_choices_match_oracle(dev, lanes, gather):
         check_pairs(sl, X.cpu().numpy(), res, 4, 1)
         for bad in (gbcg.cg_batch_tuning(inner_tol=3e-3, gather_tiles=0, lanes_per_row=3),
                     gbcg.cg_batch_tuning(inner_tol=0.0, gather_tiles=0, lanes_per_row=1),
-                    gbcg.cg_batch_tuning(inner_tol=1e-3, gather_tiles=2, lanes_per_row=1)):
+                    gbcg.cg_batch_tuning(inner_tol=1e-3, gather_tiles=2, lanes_per_row=1),
+                    gbcg.cg_batch_tuning(inner_tol=1e-3, gather_tiles=0, lanes_per_row=1, static_split=2)):
             assert gbcg.cg_batch_set_tuning(bs.h, bad) == gbcg.CG_EINVAL
