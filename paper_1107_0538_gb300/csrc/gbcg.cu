@@ -526,13 +526,14 @@ __device__ __forceinline__ void grid_totals_1k(const Params &P, int set, double 
 // Entries k0 <= k < k1 of the slice (k1 < 0: to the slice width), in
 // batches of U entries (all loads of a batch in flight before its FMAs),
 // then of kSellUnroll, then one at a time.
+// sell_slice_sum_at takes the slice's first entry a and its width wt (a
+// caller that keeps them saves the two dependent loads of M.ptr per call).
 template <int U = kSellUnroll>
-__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init,
-                                                 int k0 = 0, int k1 = -1) {
+__device__ __forceinline__ double sell_slice_sum_at(const SellMatrix &M, int t, long long a, int wt, const double *x,
+                                                    double init, int k0 = 0, int k1 = -1) {
     const int lane = threadIdx.x & 31;
     const bool st = M.stream != 0;
-    const long long a = M.ptr[t];
-    const int w = k1 >= 0 ? k1 : (int)((M.ptr[t + 1] - a) >> 5);
+    const int w = k1 >= 0 ? k1 : wt;
     const int row = t * 32 + lane;
     const double *vv = M.vals + a + lane;
     double s = init;
@@ -591,6 +592,13 @@ __device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, con
     return s;
 }
 
+template <int U = kSellUnroll>
+__device__ __forceinline__ double sell_slice_sum(const SellMatrix &M, int t, const double *x, double init,
+                                                 int k0 = 0, int k1 = -1) {
+    const long long a = M.ptr[t];
+    return sell_slice_sum_at<U>(M, t, a, (int)((M.ptr[t + 1] - a) >> 5), x, init, k0, k1);
+}
+
 template <bool PRE>
 __global__ void __launch_bounds__(kSellSolveThreads, 1)
     cg_sell_kernel(Params P, SellMatrix M, const int32_t *__restrict__ cut) {
@@ -598,6 +606,8 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
     __shared__ double quarter[12];
     __shared__ double bcast[8];
     __shared__ int ctl[16];
+    __shared__ long long slice_a[kSellSolveThreads / 32];
+    __shared__ int slice_w[kSellSolveThreads / 32];
     Smem S{};
     S.red = red;
     S.bcast = bcast;
@@ -696,11 +706,18 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
         // first iteration's are added here, the others' while the barrier
         // that publishes z completes
         const int wl = has_slice ? (M.split ? M.split[t] : 0) : 0;
-        double azl = has_slice ? sell_slice_sum(M, t, zg, 0.0, 0, wl) : 0.0;
+        // the slice's first entry and width, loaded once for the whole solve
+        // and kept in shared memory (registers are at the 64 of 1024 threads)
+        if (lane == 0 && has_slice) {
+            slice_a[w] = M.ptr[t];
+            slice_w[w] = (int)((M.ptr[t + 1] - slice_a[w]) >> 5);
+        }
+        __syncwarp();
+        double azl = has_slice ? sell_slice_sum_at(M, t, slice_a[w], slice_w[w], zg, 0.0, 0, wl) : 0.0;
         for (int k = 1;; ++k) {
             // phase A: az = A z on warps 1..31 (the rest of each row, from
             // azl); the control warp decides on iteration k-1 meanwhile
-            const double az = has_slice ? sell_slice_sum(M, t, zg, azl, wl) : 0.0;
+            const double az = has_slice ? sell_slice_sum_at(M, t, slice_a[w], slice_w[w], zg, azl, wl) : 0.0;
             if (k > 1 && w == 0) {
                 double t2[NB];
                 grid_totals<NB>(P, set ^ 1, t2);
@@ -757,7 +774,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1)
                 // x is read by nothing before the end: x += alpha p leaves
                 // the critical path (p changes only in the next phase A)
                 if (own) x = fma(alpha, p, x);
-                azl = sell_slice_sum(M, t, zg, 0.0, 0, wl);
+                azl = sell_slice_sum_at(M, t, slice_a[w], slice_w[w], zg, 0.0, 0, wl);
             } else if (tid == 0) {
                 ctl[15] = grid_wait<false>(P, epoch);
             }
