@@ -102,17 +102,18 @@ def measured_peaks() -> dict:
 _COMMON = ["cg_device.cuh", "layout.h"]
 KERNEL_SOURCES = {
     "cg_solve_kernel": ["gbcg.cu", "plan.h"] + _COMMON,
-    "cg_sell_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
-    "cg_sellmem_kernel": ["gbcg.cu", "sell.cuh", "plan.h"] + _COMMON,
+    "cg_sell_kernel": ["gbcg.cu", "sell.cuh", "sellsolve.cuh", "plan.h"] + _COMMON,
+    "cg_sellmem_kernel": ["gbcg.cu", "sell.cuh", "sellsolve.cuh", "plan.h"] + _COMMON,
     "sell_spmv_kernel": ["gbcg.cu", "sell.cuh", "plan.h"],
     "cg_ir_kernel": ["gbcg.cu", "plan.h", "lowprec.h"] + _COMMON,
-    "cg_irsell_kernel": ["gbcg.cu", "sell.cuh", "plan.h", "lowprec.h"] + _COMMON,
+    "cg_irsell_kernel": ["gbcg.cu", "sell.cuh", "sellsolve.cuh", "plan.h", "lowprec.h"] + _COMMON,
     "cg_batch_kernel": ["batch.cu", "plan.h", "lowprec.h"] + _COMMON,
     "conv16_kernel": ["learn.cu"] + _COMMON,
     "conv16tc_kernel": ["learn.cu"] + _COMMON,
     "convout_kernel": ["learn.cu"] + _COMMON,
     "conv1_kernel": ["learn.cu"] + _COMMON,
     "fcg_spmv_kernel": ["learn.cu", "plan.h"] + _COMMON,
+    "fcg_sell_kernel": ["learn.cu", "sell.cuh", "sellsolve.cuh"] + _COMMON,
 }
 
 

@@ -20,7 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(_HERE)
 SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("gbcg.cu", "noalloc.cu", "batch.cu", "learn.cu")]
 DEPS = SOURCES + [os.path.join(_HERE, "csrc", f) for f in ("cg_device.cuh", "layout.h", "plan.h", "lowprec.h",
-                                                           "handle.h", "sell.cuh", "check.cuh")] + [
+                                                           "handle.h", "sell.cuh", "sellsolve.cuh",
+                                                           "check.cuh")] + [
     os.path.join(ROOT, "include", "gbcg.h")]
 OUT = os.path.join(_HERE, "libgbcg.so")
 OUT_CHECK = os.path.join(_HERE, "libgbcg_check.so")

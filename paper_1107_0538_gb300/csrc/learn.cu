@@ -42,6 +42,7 @@
 #include "gbcg.h"
 #include "handle.h"
 #include "lowprec.h"
+#include "sellsolve.cuh"
 
 using namespace gbcg;
 
@@ -224,6 +225,7 @@ struct FcgState {
     double ring[kMaxWindow + 1];
     int32_t n, iters, status, done, mode, restart, reverted_at, mode_start, maxit, window;
     unsigned int counter;
+    unsigned int bar_count, bar_gen;   // grid barrier of the fused SELL-32 kernel (resets itself)
     int32_t pad;
 };
 
@@ -712,13 +714,17 @@ __device__ __forceinline__ void finish(FcgState *st, int status) {
 // E_OUT_Z stores z = sigma D^-1/2 u, E_OUT_FCG also forms z.r and z.q and
 // takes the flexible-CG decisions (in the Jacobi fallback it forms
 // z = D^-1 r instead of running the network).
+// Four CTAs per SM (at most 64 registers a thread): while one CTA waits for
+// its staged brick the others multiply.  The B fragments are read from a
+// shared copy of the weights tap by tap, not held in registers for all taps.
 template <int EPI>
-__global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
+__global__ void __launch_bounds__(kCT, 4) convout_kernel(ConvArgs A) {
     FcgState *st = A.st;
     if (st && st->done) return;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double sred[2 * 32];
     __shared__ float su[kRows * kBX];
+    __shared__ uint2 swt[kTaps * 4];   // tap t, lane t4: channel words {2 t4, 2 t4 + 1}, {8 + 2 t4, 9 + 2 t4}
     __shared__ int sflag, sswitch;
     const Geo &G = A.G;
     const bool learned = !st || st->mode == kModeLearned;
@@ -727,14 +733,10 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     if (learned) {
         const Brick B = brick_of(G, blockIdx.x);
         stage16(G, B, A.in, sm);
-        // B operand (one real output column): this lane's words of every tap,
-        // zero in the lanes of the other seven columns
-        uint32_t bw[kTaps][2];
-        const uint32_t *wk = reinterpret_cast<const uint32_t *>(A.w);
-#pragma unroll
-        for (int t = 0; t < kTaps; ++t) {
-            bw[t][0] = g == 0 ? __ldg(wk + ((t * kCh + 2 * t4) >> 1)) : 0u;
-            bw[t][1] = g == 0 ? __ldg(wk + ((t * kCh + 8 + 2 * t4) >> 1)) : 0u;
+        if (threadIdx.x < kTaps * 4) {
+            const uint32_t *wk = reinterpret_cast<const uint32_t *>(A.w);
+            const int t = threadIdx.x >> 2, j = threadIdx.x & 3;
+            swt[threadIdx.x] = make_uint2(__ldg(wk + ((t * kCh + 2 * j) >> 1)), __ldg(wk + ((t * kCh + 8 + 2 * j) >> 1)));
         }
         cp_async_wait_all();
         __syncthreads();
@@ -745,13 +747,16 @@ __global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
         const int a_r = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
-#pragma unroll
+        // B operand (one real output column): lanes 0-3 hold the tap's
+        // weights, the lanes of the other seven columns zero
+#pragma unroll 3
         for (int t = 0; t < kTaps; ++t) {
+            const uint2 bw = g == 0 ? swt[4 * t + t4] : make_uint2(0u, 0u);
 #pragma unroll
             for (int m = 0; m < kMTiles; ++m) {
                 uint32_t a[4];
                 ldsm_x4(a, row_addr(in_base, a_row(w, m, tap_dx(t), tap_dy(t), tap_dz(t)) + a_r, a_half));
-                mma_bf16(acc[m], a, bw[t][0], bw[t][1]);
+                mma_bf16(acc[m], a, bw.x, bw.y);
             }
         }
         // u of the brick through shared memory, then one output per thread
@@ -839,35 +844,11 @@ struct VecArgs {
     double *partials;
 };
 
-// x += alpha p, r -= alpha q; r.r and r.D^-1 r; stop test, stall test.
-// The network input s = D^-1/2 r and r.D^-1 r = s.s are formed in FP32 (s is
-// stored in BF16; r.D^-1 r only scales the network input, and after a
-// switch to Jacobi-PCG it is the first rho); x, r and r.r stay FP64.
-__global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
-    FcgState *st = V.st;
-    if (st->done) return;
-    __shared__ double sred[2 * 32];
-    __shared__ double park[2 * kVT];
-    __shared__ int sflag;
-    const double alpha = st->alpha;
-    double *x = st->x;
-    double rr = 0.0;
-    float rdr = 0.0f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < V.n; i += gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, V.p[i], x[i]);
-        const double ri = fma(-alpha, V.q[i], V.r[i]);
-        V.r[i] = ri;
-        const float si = (float)ri * V.dsq32[i];
-        V.s_in[V.pidx[i]] = __float2bfloat16_rn(si);
-        rr = fma(ri, ri, rr);
-        rdr = fmaf(si, si, rdr);
-    }
-    double v[2] = {rr, (double)rdr}, tot[2];
-    cta_sum2_256(v, park, sred);
-    if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag, sred)) return;
-    // warp 0 of the last CTA: the residual-norm window for the stall test
+// Warp 0 of the CTA that holds the grid totals {r.r, r.D^-1 r} of the x, r
+// update: the iteration count, the residual-norm window of the stall test,
+// the stop and stall decisions and the network input's scale sigma.
+__device__ __forceinline__ void xr_decide(FcgState *st, const double (&tot)[2], int n) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x >= 32) return;
     const int k = st->iters + 1;
     const double rn = sqrt(tot[0]);
     const int W = st->window, RS = W + 1;
@@ -900,8 +881,63 @@ __global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
         st->mode_start = k;
         st->restart = 1;
     }
-    st->sigma = sqrt(tot[1] / (double)V.n);
+    st->sigma = sqrt(tot[1] / (double)n);
     st->sigma_inv = st->sigma > 0.0 ? 1.0 / st->sigma : 0.0;
+}
+
+// x += alpha p, r -= alpha q; r.r and r.D^-1 r; stop test, stall test.
+// The network input s = D^-1/2 r and r.D^-1 r = s.s are formed in FP32 (s is
+// stored in BF16; r.D^-1 r only scales the network input, and after a
+// switch to Jacobi-PCG it is the first rho); x, r and r.r stay FP64.
+__global__ void __launch_bounds__(kVT) fcg_xr_kernel(VecArgs V) {
+    FcgState *st = V.st;
+    if (st->done) return;
+    __shared__ double sred[2 * 32];
+    __shared__ double park[2 * kVT];
+    __shared__ int sflag;
+    const double alpha = st->alpha;
+    double *x = st->x;
+    double rr = 0.0;
+    float rdr = 0.0f;
+    // kXrBatch nodes a thread (stride apart) are loaded before any of them is
+    // stored, so their loads are in flight together; the sums still run over
+    // the thread's nodes in increasing order
+    constexpr int kXrBatch = 4;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < V.n; i0 += kXrBatch * stride) {
+        double pv[kXrBatch], xv[kXrBatch], qv[kXrBatch], rv[kXrBatch];
+        float dv[kXrBatch];
+        int sv[kXrBatch];
+#pragma unroll
+        for (int j = 0; j < kXrBatch; ++j) {
+            const int i = i0 + j * stride;
+            if (i < V.n) {
+                pv[j] = V.p[i];
+                xv[j] = x[i];
+                qv[j] = V.q[i];
+                rv[j] = V.r[i];
+                dv[j] = V.dsq32[i];
+                sv[j] = V.pidx[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kXrBatch; ++j) {
+            const int i = i0 + j * stride;
+            if (i < V.n) {
+                x[i] = fma(alpha, pv[j], xv[j]);
+                const double ri = fma(-alpha, qv[j], rv[j]);
+                V.r[i] = ri;
+                const float si = (float)ri * dv[j];
+                V.s_in[sv[j]] = __float2bfloat16_rn(si);
+                rr = fma(ri, ri, rr);
+                rdr = fmaf(si, si, rdr);
+            }
+        }
+    }
+    double v[2] = {rr, (double)rdr}, tot[2];
+    cta_sum2_256(v, park, sred);
+    if (!last_cta_totals<2>(v, V.partials, &st->counter, tot, &sflag, sred)) return;
+    if (threadIdx.x < 32) xr_decide(st, tot, V.n);
 }
 
 // ---------------------------------------------------------- SpMV kernels
@@ -1013,6 +1049,157 @@ __global__ void __launch_bounds__(kThreads, 1) fcg_spmv_kernel(Params P, FcgStat
         else st->alpha = st->rho / pq;
     } else {
         st->true_rr = tot[0];
+    }
+}
+
+// ------------------------------ SpMV step and x, r update in one launch
+// The SpMV step and the x, r update of a flexible-CG iteration as one
+// cooperative launch (one CTA of 1024 threads per SM) on the SELL-32 copy of
+// the matrix.  Warp w of CTA c takes slices cut[c] + w, + 32, ... of the CTA's
+// range, and a row is read and written by the same thread in both phases:
+//   phase A  q = A z + beta q (= A p), p = z + beta p, partial p.q
+//            -> grid barrier; every CTA adds the partials in the same order
+//               and forms the same alpha = rho / p.q
+//   phase B  x += alpha p, r -= alpha q, the network input D^-1/2 r, partial
+//            r.r and r.D^-1 r; the last CTA to finish adds the partials and
+//            takes the stop and stall decisions
+// The arithmetic of fcg_spmv_kernel<S_Q> followed by fcg_xr_kernel, with one
+// launch and one pass over p, q fewer; the SELL-32 SpMV streams each row's
+// entries in coalesced batches with no staging.
+struct FcgSellArgs {
+    Params P;             // partials (set 0: p.q; set 1: r.r, r.D^-1 r), wait bound, error block
+    SellMatrix M;
+    const int32_t *cut;   // CTA c owns slices cut[c] .. cut[c + 1] - 1
+    VecArgs V;
+};
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int *a, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(a), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_relaxed(unsigned int *a, unsigned int v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(unsigned int *a, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// A grid barrier that resets itself, for a kernel launched many times in one
+// graph.  Thread 0 of each CTA reads the generation word, then arrives on the
+// counter (acquire-release); the last to arrive clears the counter and
+// publishes the next generation (release); the others wait for it (acquire,
+// bounded by wait_ns).  The __syncthreads after the call carries the
+// ordering to the rest of the CTA.  Returns 1 when the barrier has passed.
+__device__ __forceinline__ int fcg_grid_sync(FcgState *st, unsigned long long wait_ns) {
+    const unsigned int gen = ld_acquire(&st->bar_gen);
+    if (atom_add_acq_rel(&st->bar_count, 1u) == gridDim.x - 1) {
+        st_relaxed(&st->bar_count, 0u);
+        st_release(&st->bar_gen, gen + 1u);
+        return 1;
+    }
+    if (ld_acquire(&st->bar_gen) != gen) return 1;
+    const unsigned long long t0 = global_ns();
+    unsigned int spins = 0;
+    while (ld_acquire(&st->bar_gen) == gen) {
+        if ((++spins & 63u) == 0 && global_ns() - t0 > wait_ns) return 0;
+    }
+    return 1;
+}
+
+__global__ void __launch_bounds__(kSellSolveThreads, 1) fcg_sell_kernel(FcgSellArgs F) {
+    const VecArgs &V = F.V;
+    FcgState *st = V.st;
+    if (st->done) return;   // written only by earlier kernels: the same in every CTA
+    __shared__ double red[2 * kSellSolveThreads];
+    __shared__ double quarter[8];
+    __shared__ double bcast[1];
+    __shared__ int ctl[3];
+    constexpr int kW = kSellSolveThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int t0 = F.cut[blockIdx.x] + (tid >> 5), t1 = F.cut[blockIdx.x + 1];
+    const int n = V.n;
+    // read before the barrier; CTA 0 changes restart only after it
+    const double beta = st->restart ? 0.0 : st->beta;
+    const double rho = st->rho;
+    double *const x = st->x;
+
+    // phase A: q = A z + beta q (= A p), p = z + beta p; p . q
+    double v1[1] = {0.0};
+    for (int t = t0; t < t1; t += kW) {
+        const double az = sell_slice_sum<kSellUnrollMem>(F.M, t, V.z, 0.0);
+        const int row = t * 32 + lane;
+        if (row < n) {
+            const double qi = fma(beta, V.q[row], az);
+            const double pi = fma(beta, V.p[row], V.z[row]);
+            V.q[row] = qi;
+            V.p[row] = pi;
+            v1[0] = fma(pi, qi, v1[0]);
+        }
+    }
+    block_sum_1k<1>(v1, red, quarter);
+    publish_partials<1>(F.P, 0, v1);
+    if (tid == 0) {
+        const int ok = fcg_grid_sync(st, F.P.wait_ns);
+        if (!ok) {
+            set_error(F.P.st, CG_ETIMEOUT, 3);
+            finish(st, CG_ETIMEOUT);
+        }
+        ctl[0] = ok;
+    }
+    __syncthreads();
+    if (!ctl[0]) return;
+    double sg[1];
+    grid_totals_1k<1>(F.P, 0, sg, quarter);
+    if (tid == 0) {
+        const double pq = sg[0];
+        const int go = finite_bits(pq) && pq > 0.0;
+        const double alpha = go ? rho / pq : 0.0;
+        if (blockIdx.x == 0) {
+            st->pq = pq;
+            st->restart = 0;
+            if (!finite_bits(pq)) finish(st, CG_ENAN);
+            else if (!(pq > 0.0)) finish(st, CG_EBREAKDOWN);
+            else st->alpha = alpha;
+        }
+        bcast[0] = alpha;
+        ctl[1] = go;
+    }
+    __syncthreads();
+    if (!ctl[1]) return;
+    const double alpha = bcast[0];
+
+    // phase B: x += alpha p, r -= alpha q, s = D^-1/2 r (FP32, stored in
+    // BF16 at its padded position); r.r in FP64, r.D^-1 r = s.s in FP32
+    double rr = 0.0;
+    float rdr = 0.0f;
+    for (int t = t0; t < t1; t += kW) {
+        const int row = t * 32 + lane;
+        if (row < n) {
+            const double ri = fma(-alpha, V.q[row], V.r[row]);
+            x[row] = fma(alpha, V.p[row], x[row]);
+            V.r[row] = ri;
+            const float si = (float)ri * V.dsq32[row];
+            V.s_in[V.pidx[row]] = __float2bfloat16_rn(si);
+            rr = fma(ri, ri, rr);
+            rdr = fmaf(si, si, rdr);
+        }
+    }
+    double v2[2] = {rr, (double)rdr};
+    block_sum_1k<2>(v2, red, quarter);
+    publish_partials<2>(F.P, 1, v2);
+    if (tid == 0) {
+        __threadfence();
+        ctl[2] = atomicAdd(&st->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!ctl[2]) return;
+    __threadfence();
+    if (tid < 32) {
+        double tot[2];
+        grid_totals<2>(F.P, 1, tot);
+        if (tid == 0) st->counter = 0u;
+        xr_decide(st, tot, n);
     }
 }
 
@@ -1409,6 +1596,7 @@ struct LearnCtx {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     int vgrid = 0;
+    int fused = 0;                   // 1: the SpMV step and the x, r update run as fcg_sell_kernel
 };
 
 }  // namespace gbcg
@@ -1562,10 +1750,21 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.partials = L->partials;
     convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
     const VecArgs V = vec_args(h, L);
-    // p = z + beta p and q = A z + beta q in the SpMV's epilogue (it gathers z)
-    fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, L->z, L->partials, V);
-    fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
+    if (L->fused) {
+        // SpMV step and x, r update in one cooperative launch (SELL-32)
+        FcgSellArgs F{learn_params(h, L), sell_of(h), h->sell_cut, V};
+        void *args[] = {&F};
+        cudaLaunchCooperativeKernel((const void *)fcg_sell_kernel, dim3(h->ctas), dim3(kSellSolveThreads), args, 0,
+                                    s);
+    } else {
+        // p = z + beta p and q = A z + beta q in the SpMV's epilogue (it gathers z)
+        fcg_spmv_kernel<S_Q><<<h->ctas, kThreads, kSmemBytes, s>>>(learn_params(h, L), L->st, L->z, L->partials, V);
+        fcg_xr_kernel<<<L->vgrid, kVT, 0, s>>>(V);
+    }
 }
+
+// Kernels of one flexible-CG iteration (one graph body).
+int body_kernels(const LearnCtx *L) { return L->fused ? 5 : 6; }
 
 int capture(cg_handle *h, LearnCtx *L) {
     if (L->graph) {
@@ -1839,7 +2038,7 @@ int gbcg::learn_solve(cg_handle *h, const double *b, double *x, double tol, int3
             if (e == cudaSuccess) e = cudaEventRecord(L->ev[sl], s);
             if (e != cudaSuccess) return CG_ECUDA;
             ++launched;
-            launches += 7 * kUnroll;
+            launches += body_kernels(L) * kUnroll;
         }
         if (waited == launched) break;
         const int sl = waited & 1;
@@ -1986,6 +2185,18 @@ int cg_set_learned(cg_handle *h, cg_net *net, int32_t ex, int32_t ey, int32_t ez
     const Geo &G = L->G;
     const int sms = sm_count(h->device);
     L->vgrid = std::min((G.n + kVT - 1) / kVT, 4 * sms);
+    // the fused SELL-32 kernel needs the handle's SELL-32 CTA ranges (every
+    // handle whose FP64 solve runs a SELL-32 kernel) and one resident CTA of
+    // 1024 threads per SM
+    if (h->sell_cut) {
+        int occ = 0;
+        if (cudaFuncSetAttribute((const void *)fcg_sell_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxL1) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fcg_sell_kernel, kSellSolveThreads, 0) !=
+                cudaSuccess)
+            return fail(CG_ECUDA);
+        L->fused = occ >= 1 && h->ctas <= occ * sms;
+    }
     const size_t a16 = act_count(G, kCh);
     auto &A = L->allocs;
     const int nparts = std::max({L->vgrid, G.tiles, h->ctas, h->sell_grid});

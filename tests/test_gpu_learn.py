@@ -120,10 +120,16 @@ def test_gradient_matches_oracle():
     assert np.array_equal(net.params(), th.astype(np.float32))
 
 
-def test_zero_network_falls_back_to_jacobi_pcg():
+# vectors_in_memory = False: the SpMV step and the x, r update run as one
+# cooperative SELL-32 kernel; True: as the tiled SpMV and the vector kernel
+PATHS = [pytest.param(False, id="sell_fused"), pytest.param(True, id="tiled")]
+
+
+@pytest.mark.parametrize("vim", PATHS)
+def test_zero_network_falls_back_to_jacobi_pcg(vim):
     inst = P.learn_instance(10, 20000)
     net = gbcg.Net(np.zeros(gbcg.CG_LEARN_PARAMS, dtype=np.float32))
-    s = _learned(inst, net)
+    s = _learned(inst, net, vectors_in_memory=vim)
     b = torch.tensor(inst.b, device=DEV)
     x = torch.zeros_like(b)
     info = s.solve(b, x, 1e-8)
@@ -134,11 +140,12 @@ def test_zero_network_falls_back_to_jacobi_pcg():
     assert _rel(x.cpu().numpy(), ref["x"]) <= 1e-6
 
 
-def test_learned_fcg_matches_oracle_fcg():
+@pytest.mark.parametrize("vim", PATHS)
+def test_learned_fcg_matches_oracle_fcg(vim):
     inst = P.learn_instance(10, 20001)
     th = P.learn_init_params(seed=11, noise=0.05)
     net = gbcg.Net(th)
-    s = _learned(inst, net)
+    s = _learned(inst, net, vectors_in_memory=vim)
     b = torch.tensor(inst.b, device=DEV)
     x = torch.zeros_like(b)
     info = s.solve(b, x, 1e-8)
@@ -156,11 +163,12 @@ def test_learned_fcg_matches_oracle_fcg():
     assert np.linalg.norm(xg - inst.xstar) <= np.linalg.norm(inst.b - P.csr_times(inst.A, xg)) / lam
 
 
-def test_stall_switch_matches_oracle():
+@pytest.mark.parametrize("vim", PATHS)
+def test_stall_switch_matches_oracle(vim):
     inst = P.learn_instance(10, 20002)
     th = P.learn_init_params(seed=12, noise=0.05)
     net = gbcg.Net(th)
-    s = _learned(inst, net, stall_window=5, stall_factor=1e-6)
+    s = _learned(inst, net, stall_window=5, stall_factor=1e-6, vectors_in_memory=vim)
     b = torch.tensor(inst.b, device=DEV)
     x = torch.zeros_like(b)
     info = s.solve(b, x, 1e-8)
@@ -173,10 +181,11 @@ def test_stall_switch_matches_oracle():
     assert info.relres_true <= 1.05e-8
 
 
-def test_edge_cases_and_determinism():
+@pytest.mark.parametrize("vim", PATHS)
+def test_edge_cases_and_determinism(vim):
     inst = P.learn_instance(8, 20003)
     net = gbcg.Net(P.learn_init_params(seed=13))
-    s = _learned(inst, net)
+    s = _learned(inst, net, vectors_in_memory=vim)
     b = torch.zeros(inst.A.n, dtype=torch.float64, device=DEV)
     x = torch.ones_like(b)
     info = s.solve(b, x, 1e-8)
