@@ -105,7 +105,12 @@ constexpr size_t kStage1 = ((size_t)kStaged * 2 + 15) / 16 * 16;
 constexpr size_t kDyTile = (size_t)kBX * kRows * 32;
 size_t conv16_smem(const Geo &) { return kStage16 + (size_t)kTaps * kCh * kCh * 2; }
 size_t conv1_smem(const Geo &) { return kStage1; }
-size_t convout_smem(const Geo &) { return kStage16; }
+// the 16 -> 1 convolution stages its input rows 32 bytes apart more: a row
+// is 152 words, 24 mod 32, so 4 consecutive rows start 8 banks apart
+constexpr int kOutRowBytes = kSX * 32 + 32;
+static_assert(kOutRowBytes % 16 == 0, "16-byte aligned staged rows");
+constexpr size_t kOutStage = (size_t)kSY * kSZ * kOutRowBytes;   // one staged brick
+size_t convout_smem(const Geo &) { return 2 * kOutStage; }          // two: the next brick loads meanwhile
 size_t wgrad16_smem(const Geo &) { return kStage16 + kDyTile; }
 size_t wgrad1_smem(const Geo &) { return kStage1 + kDyTile + (size_t)(kCT / 32) * 16 * 32 * 4; }
 
@@ -118,6 +123,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -709,84 +715,212 @@ __device__ __forceinline__ void finish(FcgState *st, int status) {
 }
 
 // ------------------------------------------------ 16 -> 1 convolution
-// u[p] = sum_{t, c} K[t][c] x[c, p + off(t)] (K packed [27][16]); one real
-// output column of an n8 MMA.  EPI: E_OUT_U stores u (FP32, node order),
-// E_OUT_Z stores z = sigma D^-1/2 u, E_OUT_FCG also forms z.r and z.q and
-// takes the flexible-CG decisions (in the Jacobi fallback it forms
-// z = D^-1 r instead of running the network).
-// Four CTAs per SM (at most 64 registers a thread): while one CTA waits for
-// its staged brick the others multiply.  The B fragments are read from a
-// shared copy of the weights tap by tap, not held in registers for all taps.
+// u[p] = sum_{t, c} K[t][c] x[c, p + off(t)] (K packed [27][16]).  EPI:
+// E_OUT_U stores u (FP32, node order), E_OUT_Z stores z = sigma D^-1/2 u,
+// E_OUT_FCG also forms z.r and z.q and takes the flexible-CG decisions (in
+// the Jacobi fallback it forms z = D^-1 r instead of running the network).
+//
+// With one output channel this is 432 multiply-adds per node, and as a
+// tensor-core GEMM each output would need its own 27 A fragments (864 bytes
+// of shared memory) for one real column of the product.  So it runs on the
+// FP32 pipe (packed f32x2 FMAs, two channels an instruction),
+// register-blocked: the 4 lanes of a quad split the 16 input channels (4
+// each) and own 8 consecutive x outputs of one brick row, and
+// for each (dy, dz) they walk the 10 staged positions of the input row once:
+// every loaded input feeds up to three outputs (dx = -1, 0, 1) from
+// registers.  The quad then adds its four channel partials (a butterfly:
+// the same bits in every lane).  Input rows are staged 608 bytes apart (18
+// positions of 32 bytes plus 32), so the 32-byte pieces of the 4 rows a warp
+// reads at once fall on disjoint groups of 8 banks: a warp's load takes the
+// minimum two wavefronts (the shared-memory pipe bounds this kernel).  The kernel is persistent: a CTA loops over its share of
+// the bricks with two staging buffers, so the copies of the next brick run
+// while the current one is multiplied, the weights are read once per CTA and
+// each CTA publishes one partial of z.r and z.q.
+// Stages a brick's 16-channel input rows with the TMA unit: one 1-D bulk
+// copy per staged row (18 positions, 576 contiguous bytes of the padded
+// grid), completing on bar.  Thread r < kSY kSZ issues row r (or zero-fills
+// it when the row lies past the padded grid); thread 0 also arrives on bar
+// with the bytes expected.  The proxy fence orders the buffer's earlier
+// reads and plain stores before the copy overwrites it.
+__device__ __forceinline__ void stage16_rows_tma(const Geo &G, const Brick &B, const __nv_bfloat16 *src,
+                                                 unsigned char *sm, uint64_t *bar) {
+    const int ly = max(0, min(kSY, G.py - B.y0)), lz = max(0, min(kSZ, G.pz - B.z0));   // live rows per axis
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)(ly * lz * kSX * 32));
+    const int r = threadIdx.x;
+    if (r < kSY * kSZ) {
+        const int ys = r % kSY, zs = r / kSY;
+        unsigned char *dst = sm + r * kOutRowBytes;
+        long long pos0;
+        if (staged_row(G, B, ys, zs, pos0)) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_load_1d(dst, src + pos0 * kCh, kSX * 32, bar, false);
+        } else {
+            for (int c = 0; c < kSX * 2; ++c) reinterpret_cast<uint4 *>(dst)[c] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+// Two BF16 values (low, high half) as two FP32 values in one 64-bit register
+// pair, and the packed FP32 FMA d = a * b + c on such pairs (two IEEE
+// round-to-nearest FMAs in one instruction).
+__device__ __forceinline__ uint64_t bf16x2_f32x2(uint32_t v) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(v << 16), "r"(v & 0xffff0000u));
+    return d;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// A lane's two output nodes x, x + 1 of a brick row (node index i0 of the
+// first) and the epilogue operands the 16 -> 1 convolution needs for them;
+// nodes past the grid (or no brick: live = false) load nothing and get zeros.
+struct OutNodes {
+    int i0;
+    bool ok0, ok1;
+    float d0, d1;
+    double r0, r1, q0, q1;
+};
 template <int EPI>
-__global__ void __launch_bounds__(kCT, 4) convout_kernel(ConvArgs A) {
+__device__ __forceinline__ OutNodes out_nodes(const ConvArgs &A, const Brick &B, int xh, int oy, int oz, int j4,
+                                              bool live) {
+    const Geo &G = A.G;
+    OutNodes o{};
+    const int ox = B.x0 + xh * 8 + 2 * j4, gy = B.y0 + oy, gz = B.z0 + oz;
+    const bool rowok = live && gy < G.ny && gz < G.nz;
+    o.ok0 = rowok && ox < G.nx;
+    o.ok1 = rowok && ox + 1 < G.nx;
+    o.i0 = ox + G.nx * (gy + G.ny * gz);
+    if (EPI != E_OUT_U) {
+        if (o.ok0) o.d0 = __ldg(A.dsq32 + o.i0);
+        if (o.ok1) o.d1 = __ldg(A.dsq32 + o.i0 + 1);
+    }
+    if (EPI == E_OUT_FCG) {
+        if (o.ok0) {
+            o.r0 = __ldcg(A.r + o.i0);
+            o.q0 = __ldcg(A.q + o.i0);
+        }
+        if (o.ok1) {
+            o.r1 = __ldcg(A.r + o.i0 + 1);
+            o.q1 = __ldcg(A.q + o.i0 + 1);
+        }
+    }
+    return o;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kCT) convout_kernel(ConvArgs A) {
     FcgState *st = A.st;
     if (st && st->done) return;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ double sred[2 * 32];
-    __shared__ float su[kRows * kBX];
-    __shared__ uint2 swt[kTaps * 4];   // tap t, lane t4: channel words {2 t4, 2 t4 + 1}, {8 + 2 t4, 9 + 2 t4}
+    __shared__ float4 swt[kTaps * 4];   // tap t, channels 4 j .. 4 j + 3 at swt[4 t + j]
+    __shared__ __align__(8) uint64_t sbar[2];   // TMA completion of the two staging buffers
     __shared__ int sflag, sswitch;
     const Geo &G = A.G;
     const bool learned = !st || st->mode == kModeLearned;
     double dzr = 0.0, dzq = 0.0;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t4 = lane & 3;
     if (learned) {
-        const Brick B = brick_of(G, blockIdx.x);
-        stage16(G, B, A.in, sm);
         if (threadIdx.x < kTaps * 4) {
-            const uint32_t *wk = reinterpret_cast<const uint32_t *>(A.w);
-            const int t = threadIdx.x >> 2, j = threadIdx.x & 3;
-            swt[threadIdx.x] = make_uint2(__ldg(wk + ((t * kCh + 2 * j) >> 1)), __ldg(wk + ((t * kCh + 8 + 2 * j) >> 1)));
+            const uint2 v = __ldg(reinterpret_cast<const uint2 *>(A.w) + threadIdx.x);   // 4 BF16 weights
+            swt[threadIdx.x] = make_float4(bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y));
         }
-        cp_async_wait_all();
-        __syncthreads();
-        const uint32_t in_base = smem_u32(sm);
-        float acc[kMTiles][4];
-#pragma unroll
-        for (int m = 0; m < kMTiles; ++m)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[m][k] = 0.0f;
-        const int a_r = (lane & 7) + ((lane >> 3) & 1) * 8, a_half = lane >> 4;
-        // B operand (one real output column): lanes 0-3 hold the tap's
-        // weights, the lanes of the other seven columns zero
-#pragma unroll 3
-        for (int t = 0; t < kTaps; ++t) {
-            const uint2 bw = g == 0 ? swt[4 * t + t4] : make_uint2(0u, 0u);
-#pragma unroll
-            for (int m = 0; m < kMTiles; ++m) {
-                uint32_t a[4];
-                ldsm_x4(a, row_addr(in_base, a_row(w, m, tap_dx(t), tap_dy(t), tap_dz(t)) + a_r, a_half));
-                mma_bf16(acc[m], a, bw.x, bw.y);
-            }
-        }
-        // u of the brick through shared memory, then one output per thread
-        if (t4 == 0) {
-#pragma unroll
-            for (int m = 0; m < kMTiles; ++m)
-#pragma unroll
-                for (int hr = 0; hr < 2; ++hr)
-                    su[((w >> 1) * kBY + 4 * (w & 1) + m) * kBX + g + 8 * hr] = acc[m][2 * hr];
-        }
-        __syncthreads();
-        // z = sigma D^-1/2 u in FP32 (u is the output of BF16 products; FP32
-        // adds nothing to its error), widened for the FP64 dot products
+        // quad Q = thread / 4 owns outputs x = 8 (Q & 1) .. + 7 of brick row
+        // Q / 2 (y = row mod kBY, z = row / kBY); lane j = thread mod 4 adds
+        // input channels 4 j .. 4 j + 3 and finishes outputs 2 j and 2 j + 1
+        const int j4 = threadIdx.x & 3, quad = threadIdx.x >> 2;
+        const int xh = quad & 1, brow = quad >> 1;
+        const int oy = brow % kBY, oz = brow / kBY;
         const float sigma = EPI == E_OUT_U ? 1.0f : (float)(st ? st->sigma : A.sigma[0]);
-        for (int idx = threadIdx.x; idx < kRows * kBX; idx += blockDim.x) {
-            const int row = idx / kBX, xr = idx - row * kBX;
-            const int x = B.x0 + xr, y = B.y0 + row % kBY, z = B.z0 + row / kBY;
-            if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
-            const int i = x + G.nx * (y + G.ny * z);
-            const float u = su[idx];
-            if (EPI == E_OUT_U) {
-                A.u[i] = u;
-            } else {
-                const double zi = (double)(sigma * A.dsq32[i] * u);
-                A.z[i] = zi;
-                if (EPI == E_OUT_FCG) {
-                    dzr = fma(zi, A.r[i], dzr);
-                    dzq = fma(zi, A.q[i], dzq);
+        // the CTA's bricks b = blockIdx.x, + gridDim.x, ...: brick k is
+        // multiplied from buffer k mod 2 while brick k + 1 is staged into the
+        // other one, and the epilogue operands of a lane's two nodes are
+        // loaded one brick ahead
+        const int nb = G.tiles;
+        int b = blockIdx.x;
+        if (threadIdx.x == 0) {
+            mbar_init(&sbar[0], 1);
+            mbar_init(&sbar[1], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (b < nb) stage16_rows_tma(G, brick_of(G, b), A.in, sm, &sbar[0]);
+        OutNodes nd = out_nodes<EPI>(A, brick_of(G, b), xh, oy, oz, j4, b < nb);
+        for (int k = 0; b < nb; ++k, b += gridDim.x) {
+            const unsigned char *cur = sm + (size_t)(k & 1) * kOutStage;
+            const int bn = b + gridDim.x;
+            if (bn < nb) stage16_rows_tma(G, brick_of(G, bn), A.in, sm + (size_t)((k + 1) & 1) * kOutStage,
+                                          &sbar[(k + 1) & 1]);
+            // brick b has landed (use k / 2 of its buffer's barrier); brick bn
+            // may still be in flight
+            if (!mbar_wait_bounded(&sbar[k & 1], (uint32_t)((k >> 1) & 1), A.wait_ns)) {
+                // report, then give the copies in flight a second bounded wait
+                if (threadIdx.x == 0) {
+                    if (st) finish(st, CG_ETIMEOUT);
+                    if (A.err) atomicExch(A.err, CG_ETIMEOUT);
+                }
+                mbar_wait_bounded(&sbar[k & 1], (uint32_t)((k >> 1) & 1), A.wait_ns);
+                if (bn < nb) mbar_wait_bounded(&sbar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), A.wait_ns);
+                return;
+            }
+            __syncthreads();   // the zero-filled rows (plain stores) too
+            // two FP32 partial sums per output (even and odd input channels),
+            // one packed f32x2 FMA per channel pair
+            uint64_t acc2[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc2[i] = 0ull;
+            const unsigned char *in0 = cur + (size_t)(xh * 8) * 32 + j4 * 8;
+            const ulonglong2 *wt = reinterpret_cast<const ulonglong2 *>(swt) + j4;
+#pragma unroll
+            for (int g9 = 0; g9 < 9; ++g9) {
+                const int dy = g9 % 3 - 1, dz = g9 / 3 - 1;
+                // taps (dx, dy, dz), dx = -1, 0, 1: 3 g9, 3 g9 + 1, 3 g9 + 2
+                const ulonglong2 wm = wt[4 * (3 * g9)], w0 = wt[4 * (3 * g9 + 1)], wp = wt[4 * (3 * g9 + 2)];
+                const unsigned char *in = in0 + ((oy + 1 + dy) + kSY * (oz + 1 + dz)) * kOutRowBytes;
+#pragma unroll
+                for (int j = 0; j < 10; ++j) {
+                    // staged x = 8 xh + j feeds output i = j - 1 - dx
+                    const uint2 v = *reinterpret_cast<const uint2 *>(in + j * 32);
+                    const uint64_t a01 = bf16x2_f32x2(v.x), a23 = bf16x2_f32x2(v.y);
+                    if (j <= 7) acc2[j] = ffma2(wm.y, a23, ffma2(wm.x, a01, acc2[j]));
+                    if (j >= 1 && j <= 8) acc2[j - 1] = ffma2(w0.y, a23, ffma2(w0.x, a01, acc2[j - 1]));
+                    if (j >= 2) acc2[j - 2] = ffma2(wp.y, a23, ffma2(wp.x, a01, acc2[j - 2]));
                 }
             }
+            float acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                acc[i] = __uint_as_float((uint32_t)acc2[i]) + __uint_as_float((uint32_t)(acc2[i] >> 32));
+            // the quad's channel partials: a butterfly over its 4 lanes
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1);
+                acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 2);
+            }
+            // z = sigma D^-1/2 u in FP32 (u is the output of BF16 products;
+            // FP32 adds nothing to its error), widened for the FP64 dots
+            const float u0 = j4 == 0 ? acc[0] : j4 == 1 ? acc[2] : j4 == 2 ? acc[4] : acc[6];
+            const float u1 = j4 == 0 ? acc[1] : j4 == 1 ? acc[3] : j4 == 2 ? acc[5] : acc[7];
+            if (EPI == E_OUT_U) {
+                if (nd.ok0) A.u[nd.i0] = u0;
+                if (nd.ok1) A.u[nd.i0 + 1] = u1;
+            } else {
+                const double z0 = nd.ok0 ? (double)(sigma * nd.d0 * u0) : 0.0;
+                const double z1 = nd.ok1 ? (double)(sigma * nd.d1 * u1) : 0.0;
+                if (nd.ok0) A.z[nd.i0] = z0;
+                if (nd.ok1) A.z[nd.i0 + 1] = z1;
+                if (EPI == E_OUT_FCG) {
+                    // nodes past the grid have z = r = q = 0: they add 0
+                    dzr = fma(z1, nd.r1, fma(z0, nd.r0, dzr));
+                    dzq = fma(z1, nd.q1, fma(z0, nd.q0, dzq));
+                }
+            }
+            nd = out_nodes<EPI>(A, brick_of(G, bn), xh, oy, oz, j4, bn < nb);
+            __syncthreads();   // buffer k mod 2 is staged again for brick k + 2
         }
     } else {
         const int n = G.n;
@@ -1609,6 +1743,18 @@ int sm_count(int dev) {
     return sms > 0 ? sms : 1;
 }
 
+// CTAs of a 16 -> 1 convolution launch: persistent, as many as are resident
+// at once (each loops over its share of the bricks), at most one per brick.
+template <int EPI>
+int convout_grid(const Geo &G) {
+    int dev = 0, occ = 0;
+    cudaGetDevice(&dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, convout_kernel<EPI>, kCT, convout_smem(G)) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    return std::max(1, std::min(G.tiles, occ * sm_count(dev)));
+}
+
 template <class T>
 int ctx_alloc(std::vector<void *> &allocs, T **p, size_t count, bool zero = true) {
     *p = nullptr;
@@ -1748,7 +1894,7 @@ void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     A.q = L->q;
     A.dinv = h->dinv;
     A.partials = L->partials;
-    convout_kernel<E_OUT_FCG><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    convout_kernel<E_OUT_FCG><<<convout_grid<E_OUT_FCG>(G), kCT, convout_smem(G), s>>>(A);
     const VecArgs V = vec_args(h, L);
     if (L->fused) {
         // SpMV step and x, r update in one cooperative launch (SELL-32)
@@ -1892,7 +2038,7 @@ void enqueue_sample(cg_net *net, cg_handle *h, const float *r, const float *e) {
     A.in = net->k1;
     A.w = net->d.k1t;
     A.u = net->u;
-    convout_kernel<E_OUT_U><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    convout_kernel<E_OUT_U><<<convout_grid<E_OUT_U>(G), kCT, convout_smem(G), s>>>(A);
     // loss: v = u - e_hat, w = A_hat v
     loss_prep_kernel<<<vg, kVT, 0, s>>>(T);
     spmv_store_kernel<<<h->sell_grid, kSellThreads, 0, s>>>(sell_of(h), net->t, net->y);
@@ -2272,7 +2418,7 @@ int cg_precond_apply(cg_handle *h, const double *r, double *z) {
     A.in = L->k1;
     A.w = L->net->d.k1t;
     A.z = z;
-    convout_kernel<E_OUT_Z><<<G.tiles, kCT, convout_smem(G), s>>>(A);
+    convout_kernel<E_OUT_Z><<<convout_grid<E_OUT_Z>(G), kCT, convout_smem(G), s>>>(A);
     int err = 0;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(&err, L->conv_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
