@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -1956,7 +1957,7 @@ int cg_create(const cg_csr *A, const cg_opts *opts_in, void *stream, cg_handle *
     return CG_OK;
 }
 
-int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+static int solve_device(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
     NvtxRange nvtx("gbcg.solve");
     int rc = check_solve_args(h, b, x, tol);
     if (rc != CG_OK) return rc;
@@ -1979,7 +1980,7 @@ int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit
     return finish_solve(h, info);
 }
 
-int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+static int solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
     NvtxRange nvtx("gbcg.solve_host");
     int rc = check_solve_args(h, b, x, tol);
     if (rc != CG_OK) return rc;
@@ -2004,6 +2005,34 @@ int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t 
     if (cudaMemcpyAsync(x, h->x_dev, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
         return CG_ECUDA;
     return finish_solve(h, info);
+}
+
+// info->status is the return code whether or not the solve ran: a call that
+// fails before the solve (bad arguments, a CUDA error) leaves a result with
+// that status and nothing else.
+static constexpr int32_t kInfoUnset = INT32_MIN;
+static void settle_info(cg_info *info, int rc) {
+    if (!info) return;
+    if (info->status == kInfoUnset) {
+        *info = cg_info{};
+        info->relres_true = -1.0;
+        info->reverted_at = -1;
+    }
+    info->status = rc;
+}
+
+int cg_solve(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    if (info) info->status = kInfoUnset;
+    const int rc = solve_device(h, b, x, tol, maxit, info);
+    settle_info(info, rc);
+    return rc;
+}
+
+int cg_solve_host(cg_handle *h, const double *b, double *x, double tol, int32_t maxit, cg_info *info) {
+    if (info) info->status = kInfoUnset;
+    const int rc = solve_host(h, b, x, tol, maxit, info);
+    settle_info(info, rc);
+    return rc;
 }
 
 int cg_spmv(cg_handle *h, const double *x, double *y) {

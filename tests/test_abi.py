@@ -157,6 +157,11 @@ def test_null_handles():
     gbcg.cg_destroy(None)  # no-op
     rc, info = gbcg.cg_solve(0, 0, 0, 1e-8, 0)
     assert rc == gbcg.CG_EINVAL
+    # a call that fails before the solve still reports its code in info
+    assert info.status == gbcg.CG_EINVAL and info.iters == 0 and info.launches == 0
+    assert info.relres_true == -1.0 and info.reverted_at == -1
+    rc, info = gbcg.cg_solve_host(0, 0, 0, 1e-8, 0)
+    assert rc == gbcg.CG_EINVAL and info.status == gbcg.CG_EINVAL
     assert gbcg.cg_spmv(0, 0, 0) == gbcg.CG_EINVAL
     L = gbcg.lib()
     assert L.cg_create(None, None, None, None) == gbcg.CG_EINVAL
