@@ -1225,9 +1225,11 @@ __device__ __forceinline__ void st_release(unsigned int *a, unsigned int v) {
 // publishes the next generation (release); the others wait for it (acquire,
 // bounded by wait_ns).  The __syncthreads after the call carries the
 // ordering to the rest of the CTA.  Returns 1 when the barrier has passed.
-__device__ __forceinline__ int fcg_grid_sync(FcgState *st, unsigned long long wait_ns) {
+// phantom (a test knob, 0 in use) counts CTAs that never arrive, so that the
+// waits run out.
+__device__ __forceinline__ int fcg_grid_sync(FcgState *st, unsigned long long wait_ns, int phantom) {
     const unsigned int gen = ld_acquire(&st->bar_gen);
-    if (atom_add_acq_rel(&st->bar_count, 1u) == gridDim.x - 1) {
+    if (atom_add_acq_rel(&st->bar_count, 1u) == gridDim.x - 1 + (unsigned)phantom) {
         st_relaxed(&st->bar_count, 0u);
         st_release(&st->bar_gen, gen + 1u);
         return 1;
@@ -1274,7 +1276,7 @@ __global__ void __launch_bounds__(kSellSolveThreads, 1) fcg_sell_kernel(FcgSellA
     block_sum_1k<1>(v1, red, quarter);
     publish_partials<1>(F.P, 0, v1);
     if (tid == 0) {
-        const int ok = fcg_grid_sync(st, F.P.wait_ns);
+        const int ok = fcg_grid_sync(st, F.P.wait_ns, F.P.phantom);
         if (!ok) {
             set_error(F.P.st, CG_ETIMEOUT, 3);
             finish(st, CG_ETIMEOUT);

@@ -181,6 +181,24 @@ def test_stall_switch_matches_oracle(vim):
     assert info.relres_true <= 1.05e-8
 
 
+def test_fused_barrier_timeout_reports_status():
+    """The grid barrier of the fused SpMV-update kernel, made to wait for a CTA
+    that never arrives, gives up after the wait limit: the solve reports
+    CG_ETIMEOUT, and the next solve on the same network and context works."""
+    inst = P.learn_instance(8, 20003)
+    net = gbcg.Net(P.learn_init_params(seed=13))
+    b = torch.tensor(inst.b, device=DEV)
+    s = _learned(inst, net, wait_limit_s=2e-3, debug_phantom_arrivals=1)
+    x = torch.zeros_like(b)
+    info = s.solve(b, x, 1e-8)
+    assert info.status == gbcg.CG_ETIMEOUT, info.as_dict()
+    s.close()
+    s = _learned(inst, net)
+    x = torch.zeros_like(b)
+    info = s.solve(b, x, 1e-8)
+    assert info.status == gbcg.CG_OK and info.relres_true <= 1.05e-8
+
+
 @pytest.mark.parametrize("vim", PATHS)
 def test_edge_cases_and_determinism(vim):
     inst = P.learn_instance(8, 20003)
