@@ -10,22 +10,28 @@
 //   padded node (x+1, y+1, z+1), x fastest, (nx+2)(ny+2)(nz+2) positions plus
 //   a zero tail; a 16-channel BF16 activation is 32 bytes per position.
 //
-// A convolution is an implicit GEMM on the tensor cores (mma.sync m16n8k16,
-// BF16 in, FP32 accumulate).  A CTA (8 warps) computes a brick of 16 x 8 x 4
-// output nodes; an M-tile is one x-row of the brick (16 consecutive nodes),
-// so each of the 27 taps reads 16 consecutive rows of the staged input (a
-// constant shift).  The brick's input with its one-node halo (18 x 10 x 6
-// positions, 35 KB for 16 channels) is staged once into shared memory with a
-// bank-conflict-free swizzle of the two 16-byte halves of each row; outputs
-// past the grid (ragged bricks) are computed and dropped, so every store
-// goes to an interior node and the zero halo is never overwritten.
+// The convolutions take BF16 inputs and accumulate in FP32.  The training
+// convolutions and C1 are implicit GEMMs on mma.sync m16n8k16: a CTA (8
+// warps) computes a brick of 16 x 8 x 4 output nodes; an M-tile is one x-row
+// of the brick (16 consecutive nodes), so each of the 27 taps reads 16
+// consecutive rows of the staged input (a constant shift).  The brick's
+// input with its one-node halo (18 x 10 x 6 positions, 35 KB for 16
+// channels) is staged once into shared memory with a bank-conflict-free
+// swizzle of the two 16-byte halves of each row; outputs past the grid
+// (ragged bricks) are computed and dropped, so every store goes to an
+// interior node and the zero halo is never overwritten.  The solve's 16 -> 16
+// convolutions run on tcgen05 (conv16tc_kernel) and its 16 -> 1 convolution
+// on the FP32 pipe (convout_kernel).
 //
-// Flexible CG runs as a CUDA graph of kUnroll iterations of six kernels
-// (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, SpMV of z with the
-// p = z + beta p and q = A z + beta q updates + p.q, x/r update + stop
-// test); scalars are decided by the last CTA to finish each
-// reducing kernel (fixed-order sums: bitwise reproducible) and kept in a
-// device state block; kernels return at once after the solve is done.
+// Flexible CG runs as a CUDA graph of kUnroll iterations of five kernels
+// (conv C1, conv C2, conv C2^T, conv C1^T + z + dots, and one cooperative
+// kernel for the SpMV of z with the p = z + beta p and q = A z + beta q
+// updates, p.q, the x, r update and the stop test); handles without SELL-32
+// CTA ranges run the last as two kernels (the tiled SpMV, then the x, r
+// update).  Scalars are decided by the last CTA to finish each reducing
+// kernel, or by every CTA after the grid barrier (fixed-order sums: bitwise
+// reproducible), and kept in a device state block; kernels return at once
+// after the solve is done.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -1863,7 +1869,7 @@ VecArgs vec_args(cg_handle *h, LearnCtx *L) {
     return V;
 }
 
-// One flexible-CG iteration: six launches.
+// One flexible-CG iteration: five launches (six without the fused kernel).
 void enqueue_body(cg_handle *h, LearnCtx *L, cudaStream_t s) {
     const Geo &G = L->G;
     const cg_net *net = L->net;
