@@ -36,6 +36,7 @@
 // TMA-staged tiles (whose plan cg_create builds on the host).
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -278,10 +279,34 @@ bool on_device(const void *p, int dev) {
     return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
+int solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit, void *stream,
+                  cg_info *info);
+
 }  // namespace
 
+// info->status is the return code whether or not the solve ran: a call
+// rejected before the solve leaves a result with that status and nothing
+// else (relres_true and reverted_at -1).
 extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit,
                                 void *stream, cg_info *info) {
+    constexpr int32_t kUnset = INT32_MIN;
+    if (info) info->status = kUnset;
+    const int rc = solve_noalloc(A, b, x, tol, maxit, stream, info);
+    if (info) {
+        if (info->status == kUnset) {
+            *info = cg_info{};
+            info->relres_true = -1.0;
+            info->reverted_at = -1;
+        }
+        info->status = rc;
+    }
+    return rc;
+}
+
+namespace {
+
+int solve_noalloc(const cg_csr *A, const double *b, double *x, double tol, int32_t maxit, void *stream,
+                  cg_info *info) {
     if (!A || A->mem != CG_MEM_DEVICE) return CG_EINVAL;
     if (A->n < 0 || A->n > CG_NOALLOC_MAX_N || A->nnz < 0 || A->nnz > (int64_t)INT32_MAX) return CG_EINVAL;
     if (!(tol >= 0.0) || !std::isfinite(tol)) return CG_EINVAL;
@@ -341,3 +366,5 @@ extern "C" int cg_solve_noalloc(const cg_csr *A, const double *b, double *x, dou
     }
     return s.status;
 }
+
+}  // namespace

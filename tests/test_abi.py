@@ -181,8 +181,9 @@ def test_product_path_does_not_import_oracle():
 
 def test_noalloc_rejects_sizes_beyond_its_workspace_without_gpu():
     c = gbcg.cg_csr(gbcg.CG_NOALLOC_MAX_N + 1, 0, 1, 1, 1, gbcg.CG_MEM_DEVICE)
-    rc, _ = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
+    rc, info = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
     assert rc == gbcg.CG_EINVAL
+    assert info.status == gbcg.CG_EINVAL and info.iters == 0 and info.reverted_at == -1
     c = gbcg.cg_csr(10, 0, 1, 1, 1, gbcg.CG_MEM_HOST)  # host arrays are not accepted
     rc, _ = gbcg.cg_solve_noalloc(c, 8, 16, 1e-8, 0, None)
     assert rc == gbcg.CG_EINVAL
